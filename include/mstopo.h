@@ -1,0 +1,175 @@
+/*
+ * mstopo -- two-level spectral-MsFEM preconditioned CG for SIMP Q4 plane elasticity on one
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Method: Alexandersen & Lazarov, "Robust topology optimisation of microstructural details
+ * without length scale separation -- using a spectral coarse basis preconditioner"
+ * (arXiv:1411.3923).  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ *  - Mesh: nelx x nely unit-square bilinear (Q4) elements, plane stress, unit thickness.
+ *    Node (i, j), i in [0, nelx] along x, j in [0, nely] along y (upwards).
+ *  - Nodal vectors (displacements, forces, residuals): double[nely+1][nelx+1][2],
+ *    row-major, component 0 = x, 1 = y  ("nodal layout").
+ *  - Element fields: double[nely][nelx], row-major, row 0 = bottom row ("element layout").
+ *  - Design fields: element layout of the whole mesh, or double[cell_y][cell_x] for a
+ *    periodic unit cell that is tiled over the mesh (Sec. 4.1).
+ *  - Pointers marked DEVICE must be CUDA device (or managed) memory on the handle's device;
+ *    pointers marked HOST are ordinary host memory.  The caller owns every array it passes;
+ *    the library never keeps a caller pointer beyond the call.  Inputs are read on the
+ *    handle's stream, outputs are complete when the call returns (every call synchronises
+ *    the handle's stream before returning, except where stated).
+ *  - Every call returns an mstopo_status.  No call aborts, traps or throws; on failure
+ *    mstopo_last_error(h) describes the cause.  A handle is not thread-safe.
+ *  - Dirichlet DOFs: every displacement and residual the library returns is zero there;
+ *    input vectors are read as if their Dirichlet entries were zero.
+ */
+#ifndef MSTOPO_H
+#define MSTOPO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSTOPO_OK = 0,
+  MSTOPO_INVALID_ARG = 1,     /* a size, pointer or parameter is out of range            */
+  MSTOPO_OUT_OF_MEMORY = 2,   /* a device allocation failed                               */
+  MSTOPO_CUDA_ERROR = 3,      /* a CUDA runtime call or kernel launch failed              */
+  MSTOPO_NOT_SPD = 4,         /* a Cholesky pivot or a CG curvature p^T K p was <= 0      */
+  MSTOPO_MAX_ITER = 5,        /* the solve stopped at max_iter before reaching tol        */
+  MSTOPO_NONFINITE = 6,       /* a NaN or Inf appeared in an input or an iterate          */
+  MSTOPO_TIMEOUT = 7,         /* a bounded device-side wait gave up                        */
+  MSTOPO_NOT_READY = 8        /* a prerequisite call (set_design / build) has not run      */
+} mstopo_status;
+
+typedef enum {
+  MSTOPO_FP64 = 0,   /* everything in FP64: matvec, preconditioner, Krylov vectors        */
+  MSTOPO_MIXED = 1   /* FP64 flexible CG (x, r, dot products, residual replacement, coarse
+                        solve); FP32 matvec, patch solves, restriction and prolongation   */
+} mstopo_precision;
+
+typedef enum {
+  MSTOPO_FIELD_RHO_TILDE = 0,  /* filtered design (design layout)                         */
+  MSTOPO_FIELD_RHO_BAR = 1,    /* projected density of one realisation (design layout)    */
+  MSTOPO_FIELD_YOUNG = 2       /* SIMP Young's modulus of one realisation (element layout) */
+} mstopo_field;
+
+typedef struct mstopo_handle mstopo_handle;
+
+/* Problem description (Sec. 2.1-2.2 and 2.4). */
+typedef struct {
+  int32_t nelx, nely;        /* elements along x and y; both multiples of H               */
+  double nu;                 /* Poisson's ratio, 0 <= nu < 0.5                             */
+  double E0, Emin, penal;    /* modified SIMP: E = Emin + (E0 - Emin) rho_bar^penal (Sec. 2.2) */
+  const uint8_t* fixed;      /* HOST, nodal layout of uint8: nonzero = Dirichlet DOF (u = 0) */
+  int32_t H;                 /* coarse cell edge in elements (Sec. 2.4); agglomerates are 2H x 2H */
+  int32_t n_eig;             /* eigenvectors kept per agglomerate (cap when lambda_thresh > 0), 1..16 */
+  double lambda_thresh;      /* > 0: keep only eigenvalues below it (Sec. 2.4, lambda_Omega) */
+  int32_t precision;         /* mstopo_precision                                           */
+  double tol;                /* stop when ||f - K u||_2 / ||f||_2 <= tol (true FP64 residual) */
+  int32_t max_iter;          /* flexible-CG iteration cap                                   */
+  double local_shift;        /* MIXED only: patch matrices are factorised as K_i + s diag(K_i)
+                                (s >= 0, 0 = exact local solves)                            */
+  void* stream;              /* cudaStream_t for all work of this handle, NULL = default   */
+} mstopo_problem;
+
+typedef struct {
+  int32_t n_agglomerates;     /* coarse nodes N_c                                          */
+  int32_t n_types;            /* distinct agglomerates after de-duplication (Sec. 2.4.1)    */
+  int32_t n_coarse;           /* coarse unknowns N_t                                        */
+  int32_t eig_sweeps;         /* largest number of subspace-iteration sweeps over all types */
+  double eig_residual;        /* largest ||K psi - lambda D psi||_{D^-1} over kept pairs    */
+  float ms_hash, ms_eigen, ms_patch_factor, ms_coarse, ms_total;   /* phase times (events)  */
+} mstopo_build_info;
+
+typedef struct {
+  int32_t status;             /* mstopo_status of this system                              */
+  int32_t iterations;         /* flexible-CG iterations                                    */
+  int32_t replacements;       /* FP64 residual recomputations                              */
+  double rel_residual;        /* final true ||f - K u||_2 / ||f||_2 (FP64)                  */
+  double compliance;          /* f^T u (Sec. 2.2)                                           */
+  float ms;                   /* device time of the solve (events on the handle's stream)  */
+} mstopo_solve_info;
+
+/* Create a handle for one mesh and boundary-condition set; allocates its device workspace.
+ * Errors: INVALID_ARG (sizes not multiples of H, H < 2, nelx/H < 2 or nely/H < 2, n_eig
+ * outside 1..16, nu outside [0, 0.5), Emin <= 0 or Emin > E0, fixed == NULL),
+ * OUT_OF_MEMORY, CUDA_ERROR.  *out is NULL on failure. */
+mstopo_status mstopo_create(const mstopo_problem* desc, mstopo_handle** out);
+void mstopo_destroy(mstopo_handle* h);
+const char* mstopo_last_error(const mstopo_handle* h);
+/* Degrees of freedom 2 (nelx+1)(nely+1), and the number of realisations last set. */
+int64_t mstopo_num_dofs(const mstopo_handle* h);
+int32_t mstopo_num_realisations(const mstopo_handle* h);
+
+/* Design chain (Sec. 4.3, 2.2): density filter of radius rmin (weights max(0, rmin - d),
+ * centroid distances in element units, normalised by the in-domain weight sum; periodic
+ * wrap-around on the unit cell when cell_x > 0), then one Heaviside projection per
+ * threshold eta[k] with sharpness beta, then modified SIMP moduli on the whole mesh.
+ * rho: DEVICE, n_design doubles in design layout (n_design = nelx*nely, or cell_x*cell_y
+ * with nelx % cell_x == 0 and nely % cell_y == 0).  eta: HOST, n_eta in 1..4 values in (0,1).
+ * Errors: INVALID_ARG, NONFINITE (rho has a NaN/Inf), CUDA_ERROR. */
+mstopo_status mstopo_set_design(mstopo_handle* h, const double* rho, int64_t n_design,
+                                double rmin, double beta, const double* eta, int32_t n_eta,
+                                int32_t cell_x, int32_t cell_y);
+/* Copy a design-chain field to out (DEVICE; design or element layout, see mstopo_field). */
+mstopo_status mstopo_get_field(mstopo_handle* h, int32_t field, int32_t realisation, double* out);
+
+/* Build the two-level preconditioner (Sec. 2.4, 3.2, 5.3) on the moduli of realisation
+ * ref (-1 = the dilated one, i.e. the smallest eta): agglomerate de-duplication, local
+ * generalised eigenproblems K_w psi = lambda diag(K_w) psi, coarse basis chi_i psi_j,
+ * K_c = R_c K R_c^T and its FP64 factor, and the factors of the overlapping patch matrices.
+ * info: HOST, may be NULL.  Errors: NOT_READY (no design), NOT_SPD, CUDA_ERROR. */
+mstopo_status mstopo_build_preconditioner(mstopo_handle* h, int32_t ref, mstopo_build_info* info);
+
+/* Solve K(E_k) u_k = f for realisation k (or for all realisations when realisation == -1,
+ * as one batch sharing the preconditioner, Sec. 5.3) by flexible CG from u0 (or zero).
+ * f: DEVICE nodal layout (NULL = the zero load is rejected: INVALID_ARG);
+ * u: DEVICE, n_sys nodal vectors back to back (n_sys = 1 or the number of realisations);
+ * u0: DEVICE like u, or NULL.  infos: HOST array of n_sys, may be NULL.
+ * The solution also stays in the handle for mstopo_compliance_and_sensitivity.
+ * Returns the worst status over the systems (MAX_ITER, NOT_SPD, NONFINITE, ...). */
+mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* f, double* u,
+                           const double* u0, mstopo_solve_info* infos);
+/* As mstopo_solve, with f, u (and u0) in HOST memory: the copies to and from the device
+ * are part of the call. */
+mstopo_status mstopo_solve_host(mstopo_handle* h, int32_t realisation, const double* f,
+                                double* u, const double* u0, mstopo_solve_info* infos);
+
+/* Compliances c_k = f^T u_k of the last all-realisation solve, the robust objective
+ * mean(c) + kappa std(c) (population std, Sec. 4.4), and its gradient with respect to the
+ * design: the self-adjoint element sensitivity -p (E0-Emin) rho_bar^(p-1) u_e^T K0 u_e
+ * (Sec. 4.2) chained through the projection, the periodic tiling (sum over copies,
+ * Sec. 4.1) and the filter transpose.  c: HOST [n_eta] or NULL; f_robust: HOST or NULL;
+ * dfdrho: DEVICE design layout, or NULL.  Errors: NOT_READY (no all-realisation solve). */
+mstopo_status mstopo_compliance_and_sensitivity(mstopo_handle* h, double kappa, double* c,
+                                                double* f_robust, double* dfdrho);
+
+/* ---- kernel-level entry points (verification and measurement) --------------------- */
+
+/* y = K(E_k) u on the free DOFs, matrix-free element by element (Sec. 2.1), in the given
+ * precision (MSTOPO_MIXED = FP32 arithmetic and FP32 vectors).  u, y: DEVICE nodal layout. */
+mstopo_status mstopo_apply_K(mstopo_handle* h, int32_t realisation, int32_t precision,
+                             const double* u, double* y);
+/* Same, on vectors already stored in FP32 (DEVICE, nodal layout, float).  No conversions:
+ * this is the kernel the MIXED flexible CG runs. */
+mstopo_status mstopo_apply_K_f32(mstopo_handle* h, int32_t realisation, const float* u, float* y);
+/* z = M^-1 r with the built two-level preconditioner (coarse + overlapping patch solves),
+ * in the given precision.  part: 0 = both levels, 1 = coarse only R_c^T K_c^-1 R_c r,
+ * 2 = patches only.  r, z: DEVICE nodal layout. */
+mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t part,
+                                   const double* r, double* z);
+/* Eigenpairs kept for the agglomerate of coarse node (I, J) (Sec. 2.4):
+ * lambda: HOST [n_eig]; psi: HOST [2H+1][2H+1][2][n_eig] on the agglomerate's node box
+ * whose lower-left node is ((I-1)H, (J-1)H) (entries outside the mesh are zero);
+ * *n_kept: HOST.  The vectors are normalised psi^T diag(K_w) psi = 1. */
+mstopo_status mstopo_get_eigenpairs(mstopo_handle* h, int32_t I, int32_t J, double* lambda,
+                                    double* psi, int32_t* n_kept);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSTOPO_H */

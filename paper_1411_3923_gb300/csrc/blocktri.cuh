@@ -1,0 +1,171 @@
+// Block-tridiagonal SPD factorisation and solves, one CTA per system.
+//
+// The structured sub-grid operators of the two-level preconditioner -- agglomerate and
+// patch matrices (node rows of a (2H+-1)^2 box) and the coarse matrix (coarse-node lines,
+// whose basis functions only overlap their 3x3 coarse neighbours) -- are block
+// tridiagonal: diagonal blocks A_k and sub-diagonal blocks B_k = A_{k+1,k}, nb x nb each.
+// Block Cholesky:  S_0 = A_0,  L_k = chol(S_k),  C_k = B_k L_k^-T,  S_{k+1} = A_{k+1} - C_k C_k^T.
+// Stored per line: Linv_k = L_k^-1 (dense, lower) and C_k, so that both solve sweeps are
+// dense block products with no sequential triangular substitution inside a line:
+//   forward   y_k = Linv_k (b_k - C_{k-1} y_{k-1})
+//   backward  x_k = Linv_k^T (y_k - C_k^T x_{k+1}).
+// Matrices are row-major nb x nb.  Vectors of R right-hand sides are [NL][nb][R].
+#pragma once
+#include "internal.cuh"
+
+// ------------------------------------------------------------------- factorisation (FP64)
+// S (nb x nb, global or shared) := lower Cholesky factor of S, in place.  Returns 0 on
+// success, or 1 + the failing pivot index.  Whole CTA participates.
+__device__ inline int bt_chol_inplace(double* S, int nb, int* sh_fail) {
+  if (threadIdx.x == 0) *sh_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = S[j * nb + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (*sh_fail == 0) *sh_fail = 1 + j;
+        d = 1.0;
+      }
+      S[j * nb + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double inv = 1.0 / S[j * nb + j];
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) S[i * nb + j] *= inv;
+    __syncthreads();
+    // trailing update of the lower triangle: S[i][l] -= S[i][j] S[l][j], j < l <= i
+    const int m = nb - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int i = j + 1 + t / m, l = j + 1 + t % m;
+      if (l <= i) S[i * nb + l] = fma(-S[i * nb + j], S[l * nb + j], S[i * nb + l]);
+    }
+    __syncthreads();
+  }
+  return *sh_fail;
+}
+
+// Linv := L^-1 for lower-triangular L (upper part of Linv set to 0).  One thread per column.
+__device__ inline void bt_tri_inverse(const double* L, double* Linv, int nb) {
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) Linv[i * nb + c] = 0.0;
+    for (int i = c; i < nb; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int l = c; l < i; ++l) s = fma(-L[i * nb + l], Linv[l * nb + c], s);
+      Linv[i * nb + c] = s / L[i * nb + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Factor one block-tridiagonal system.  A: [NL][nb][nb], B: [NL-1][nb][nb] (read only);
+// shift: diagonal entries of A are multiplied by (1 + shift) on free DOFs (free[k*nb+i]).
+// Outputs Linv [NL][nb][nb], C [NL-1][nb][nb]; S is an nb x nb workspace.
+// Returns 0 or 1 + (global row index) of the first non-positive pivot.
+__device__ inline int bt_factor(const double* A, const double* B, const uint8_t* free,
+                                double shift, int nb, int NL, double* Linv, double* C,
+                                double* S, int* sh_fail) {
+  const int nn = nb * nb;
+  int fail = 0;
+  for (int k = 0; k < NL; ++k) {
+    const double* Ak = A + (long long)k * nn;
+    // S = A_k (+ shift) - C_{k-1} C_{k-1}^T   (C_{k-1} = L_{k,k-1})
+    const double* Cp = k > 0 ? C + (long long)(k - 1) * nn : nullptr;
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+      int i = t / nb, l = t % nb;
+      double v = Ak[t];
+      if (i == l && free && free[k * nb + i]) v *= (1.0 + shift);
+      if (Cp && l <= i) {
+        double s = 0.0;
+        for (int q = 0; q < nb; ++q) s = fma(Cp[i * nb + q], Cp[l * nb + q], s);
+        v -= s;
+      }
+      S[t] = v;
+    }
+    __syncthreads();
+    int f = bt_chol_inplace(S, nb, sh_fail);
+    if (f && !fail) fail = k * nb + f;
+    double* Li = Linv + (long long)k * nn;
+    bt_tri_inverse(S, Li, nb);
+    if (k + 1 < NL) {
+      // C_k = B_k L_k^-T :  C[i][j] = sum_{l <= j} B[i][l] Linv[j][l]
+      const double* Bk = B + (long long)k * nn;
+      double* Ck = C + (long long)k * nn;
+      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        int i = t / nb, j = t % nb;
+        double s = 0.0;
+        for (int l = 0; l <= j; ++l) s = fma(Bk[i * nb + l], Li[j * nb + l], s);
+        Ck[t] = s;
+      }
+      __syncthreads();
+    }
+  }
+  return fail;
+}
+
+// ------------------------------------------------------------------------- solves
+// out[i][r] (+)= sign * sum_c M[i][c] v[c][r]  (TRANS: M[c][i]).  LOWER: M is lower
+// triangular (skip the zero half).  M may live in shared or global memory.
+template <typename T, bool TRANS, bool LOWER>
+__device__ __forceinline__ void bt_gemm(const T* M, const T* v, T* out, int nb, int R,
+                                        bool accumulate, T sign) {
+  for (int t = threadIdx.x; t < nb * R; t += blockDim.x) {
+    int i = t / R, r = t % R;
+    int c0 = 0, c1 = nb;
+    if (LOWER) {
+      if (TRANS) c0 = i;      // (M^T)[i][c] = M[c][i] nonzero for c >= i
+      else c1 = i + 1;        // M[i][c] nonzero for c <= i
+    }
+    T s = T(0);
+    for (int c = c0; c < c1; ++c) {
+      T m = TRANS ? M[c * nb + i] : M[i * nb + c];
+      s = fma(m, v[c * R + r], s);
+    }
+    out[t] = accumulate ? fma(sign, s, out[t]) : sign * s;
+  }
+}
+
+// In-place solve with the stored factor.  X: [NL][nb][R] (global).  Shared scratch:
+// stage (nb*nb, used when STAGE), t0, t1 (nb*R each).  Whole CTA participates.
+template <typename T, bool STAGE>
+__device__ void bt_solve(const T* __restrict__ Linv, const T* __restrict__ C, int nb, int NL,
+                         T* X, int R, T* stage, T* t0, T* t1) {
+  const int nn = nb * nb, nv = nb * R;
+  auto mat = [&](const T* M) -> const T* {
+    if (!STAGE) return M;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) stage[q] = M[q];
+    __syncthreads();
+    return stage;
+  };
+  // forward: t1 holds y_{k-1}
+  for (int k = 0; k < NL; ++k) {
+    T* Xk = X + (long long)k * nv;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    __syncthreads();
+    if (k > 0) {
+      const T* M = mat(C + (long long)(k - 1) * nn);
+      bt_gemm<T, false, false>(M, t1, t0, nb, R, true, T(-1));
+    }
+    const T* M = mat(Linv + (long long)k * nn);
+    __syncthreads();
+    bt_gemm<T, false, true>(M, t0, t1, nb, R, false, T(1));
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+  }
+  // backward: t1 holds x_{k+1}
+  for (int k = NL - 1; k >= 0; --k) {
+    T* Xk = X + (long long)k * nv;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    __syncthreads();
+    if (k + 1 < NL) {
+      const T* M = mat(C + (long long)k * nn);
+      bt_gemm<T, true, false>(M, t1, t0, nb, R, true, T(-1));
+    }
+    const T* M = mat(Linv + (long long)k * nn);
+    __syncthreads();
+    bt_gemm<T, true, true>(M, t0, t1, nb, R, false, T(1));
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+  }
+  __syncthreads();
+}

@@ -1,0 +1,178 @@
+// Internal declarations shared by the translation units of the mstopo library.
+// Layouts: nodal vectors [nely+1][nelx+1][2] (x fastest, components interleaved), element
+// fields [nely][nelx].  Everything runs on the handle's stream.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/mstopo.h"
+
+#define MSTOPO_MAX_SYS 4      // realisations solved together with one preconditioner
+#define MSTOPO_MAX_EIG 16     // eigenvectors kept per agglomerate
+#define MSTOPO_RED_BLOCKS 304 // CTAs of the fused reduction kernels (2 per SM of a GB300)
+
+// ---------------------------------------------------------------------------------------
+// Element stiffness of a unit square, unit E, plane stress, derived in closed form
+// (host, FP64).  Local node order (0,0),(1,0),(1,1),(0,1); DOF 2a = x, 2a+1 = y.
+void element_stiffness_closed_form(double nu, double K0[64]);
+
+// Coefficients of the node-centred matvec: for each of the four elements around a node
+// (LL, LR, UL, UR) the 2x2 blocks coupling the node to the element's three other nodes.
+template <typename T>
+struct StencilCoef {
+  T c[4][3][4];   // [element][other node][row-major 2x2 block]
+};
+void make_stencil(const double K0[64], StencilCoef<double>& cd, StencilCoef<float>& cf);
+
+// ---------------------------------------------------------------------------------------
+// Kernel launchers (each returns the launch status).
+cudaError_t launch_matvec_f32(const float* u, float* y, const float* E, const uint8_t* nmask,
+                              int nelx, int nely, const StencilCoef<float>& c, int nsys,
+                              long long vec_stride, long long e_stride, cudaStream_t s);
+cudaError_t launch_matvec_f64(const double* u, double* y, const double* E, const uint8_t* nmask,
+                              int nelx, int nely, const StencilCoef<double>& c, int nsys,
+                              long long vec_stride, long long e_stride, cudaStream_t s);
+
+// design chain
+cudaError_t launch_filter(const double* rho, double* rho_tilde, double* wsum, int dx, int dy,
+                          double rmin, int periodic, cudaStream_t s);
+cudaError_t launch_project(const double* rho_tilde, double* rbar, double* drbar, int n,
+                           const double* etas, int n_eta, double beta, cudaStream_t s);
+cudaError_t launch_simp(const double* rbar, double* E64, float* E32, int nelx, int nely,
+                        int dx, int dy, int periodic, int n_eta, int n_design,
+                        double E0, double Emin, double penal, cudaStream_t s);
+cudaError_t launch_sensitivity(const double* u, long long u_stride, const double* rbar,
+                               const double* drbar, int n_eta, const double* w, int nelx,
+                               int nely, int dx, int dy, int periodic, int n_design,
+                               double dE, double penal, const double* K0, double* g_fine,
+                               cudaStream_t s);
+cudaError_t launch_tile_sum(const double* g_fine, double* g_design, int nelx, int nely,
+                            int dx, int dy, cudaStream_t s);
+cudaError_t launch_filter_T(const double* g, const double* wsum, double* out, int dx, int dy,
+                            double rmin, int periodic, cudaStream_t s);
+cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s);
+
+// Krylov / vector kernels (deterministic two-stage reductions)
+cudaError_t launch_dot_partials(const double* a, const double* b, long long n, int nsys,
+                                long long stride, double* partials, cudaStream_t s);
+cudaError_t launch_dot_partials_f32(const float* a, const float* b, long long n, int nsys,
+                                    long long stride, double* partials, cudaStream_t s);
+cudaError_t launch_dot_partials_mix(const float* a, const double* b, long long n, int nsys,
+                                    long long stride, double* partials, cudaStream_t s);
+cudaError_t launch_finish_sum(const double* partials, int nsys, double* out, cudaStream_t s);
+
+// generic precision helpers
+cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t s);
+cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t s);
+cudaError_t launch_mask_copy(const double* a, double* b, const uint8_t* nmask, long long n_nodes,
+                             int nsys, long long stride, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Flexible CG driver state (krylov.cu)
+struct FcgScalars {            // per system, on the device
+  double rr;                   // ||r||^2
+  double ff;                   // ||f||^2
+  double pq, pr, zq;           // p^T q, p^T r, z^T q_prev
+  double pq_prev;              // previous p^T q
+  double alpha, beta;
+  int active;                  // 1 while iterating
+  int status;                  // mstopo_status
+  int iters;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------------------
+// Preconditioner (precond.cu)
+struct Precond {
+  int H = 0, NA = 0, NP = 0, nbA = 0, nbP = 0, ncx = 0, ncy = 0, Nc = 0, kmax = 0;
+  int n_types = 0, Nt = 0;
+  int built = 0;
+  double local_shift = 0.0;
+  std::vector<int> h_type_of_agg, h_rep_agg, h_kept, h_coff;   // host copies
+  int* d_type_of_agg = nullptr;     // [Nc]
+  int* d_kept = nullptr;            // [n_types]
+  int* d_coff = nullptr;            // [Nc+1] coarse-unknown offsets
+  int* d_perm = nullptr;            // [Nc] agglomerates sorted by type
+  int* d_grp_type = nullptr;        // [n_groups] patch-solve work items
+  int* d_grp_first = nullptr;
+  int* d_grp_count = nullptr;
+  int n_groups = 0;
+  // per-type patch factors (block tridiagonal by node rows): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
+  double* d_pLinv64 = nullptr; double* d_pC64 = nullptr;
+  float* d_pLinv32 = nullptr;  float* d_pC32 = nullptr;
+  // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
+  double* d_lambda = nullptr; double* d_psi64 = nullptr; float* d_psi32 = nullptr;
+  double* d_eigres = nullptr;       // [T] residual norms
+  int* d_eigsweeps = nullptr;       // [T]
+  // coarse problem: dense FP64 inverse of K_c [Nt][Nt]
+  double* d_Kc = nullptr;
+  double* d_Kcinv = nullptr;
+  // apply buffers
+  double* d_rc = nullptr;           // [MAX_SYS][Nt]
+  double* d_uc = nullptr;           // [MAX_SYS][Nt]
+  double* d_rcpart = nullptr;       // restriction partials
+  float* d_zp32 = nullptr;          // [MAX_SYS][Nc][NP*NP*2]
+  double* d_zp64 = nullptr;
+  // workspaces for the build
+  double* d_work = nullptr; size_t work_bytes = 0;
+  int* d_flag = nullptr;
+};
+
+struct Solver {
+  long long n = 0;                  // DOFs
+  double *x = nullptr, *r = nullptr, *f = nullptr, *tmp = nullptr;    // [MAX_SYS][n] FP64
+  double *p64 = nullptr, *q64 = nullptr, *z64 = nullptr;              // FP64 mode
+  float *p32 = nullptr, *q32 = nullptr, *z32 = nullptr, *r32 = nullptr; // MIXED mode
+  double* partials = nullptr;       // [MAX_SYS][4][RED_BLOCKS]
+  FcgScalars* sc = nullptr;         // [MAX_SYS]
+  FcgScalars* h_sc = nullptr;       // pinned host mirror
+};
+
+struct mstopo_handle {
+  mstopo_problem p{};
+  cudaStream_t s = nullptr;
+  int nelx = 0, nely = 0;
+  long long n_nodes = 0, n_dof = 0, n_el = 0;
+  std::string err;
+  double K0[64];
+  StencilCoef<double> st64;
+  StencilCoef<float> st32;
+  double* d_K0 = nullptr;
+  uint8_t* d_nmask = nullptr;       // per node: bit0 = x fixed, bit1 = y fixed
+  // design
+  int design_ready = 0, n_eta = 0, periodic = 0, dx = 0, dy = 0;
+  long long n_design = 0;
+  double etas[MSTOPO_MAX_SYS] = {0}, beta = 0, rmin = 0;
+  double *d_rho = nullptr, *d_rho_tilde = nullptr, *d_wsum = nullptr;
+  double *d_rbar = nullptr, *d_drbar = nullptr;
+  double* d_E64 = nullptr; float* d_E32 = nullptr;
+  double *d_gfine = nullptr, *d_gdesign = nullptr, *d_w = nullptr;
+  int* d_flag = nullptr;
+  // preconditioner, solver
+  Precond pc;
+  Solver sv;
+  int pc_ref = -1;
+  int u_all_ready = 0;
+  double* d_u_all = nullptr;        // [MAX_SYS][n_dof] last all-realisation solution
+  double* d_f_all = nullptr;        // load used for it
+  double* d_host_stage = nullptr;   // device staging for the host-pointer entry point
+};
+
+// precond.cu
+mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info);
+void precond_free(Precond& pc);
+// Apply z = M^-1 r for nsys systems (vectors with stride n_dof).  part: 0 both, 1 coarse,
+// 2 patches.  FP32 variant reads/writes float vectors.
+cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int nsys, int part);
+cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int nsys, int part);
+
+// krylov.cu
+mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
+                        const double* u0, mstopo_solve_info* infos);
+mstopo_status solver_alloc(mstopo_handle* h);
+void solver_free(Solver& sv);
+
+// helpers
+inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }

@@ -1,0 +1,490 @@
+// Flexible conjugate gradients in FP64 with the two-level preconditioner (paper Sec. 2.4.2:
+// K and the preconditioner are SPD, so CG applies; the paper itself uses GMRES).
+//
+// FCG(1) (Notay): with z_k = B(r_k),
+//   p_k = z_k - (z_k^T q_{k-1} / p_{k-1}^T q_{k-1}) p_{k-1},  q_k = K p_k,
+//   alpha_k = p_k^T r_k / p_k^T q_k,  x += alpha p,  r -= alpha q.
+// The explicit K-orthogonalisation against the previous direction keeps the recurrence
+// valid when B varies slightly from one application to the next (FP32 preconditioner).
+//
+// Precision modes
+//   FP64   p, q, z and every kernel in FP64.
+//   MIXED  x, r and all dot products in FP64; p, q, z stored in FP32; q = K p with the FP32
+//          difference-form matvec; the preconditioner in FP32 except the FP64 coarse solve.
+//          The recursive residual drifts from the true one by the FP32 matvec error, so the
+//          true residual f - K x is recomputed in FP64 whenever the recursive one has
+//          dropped by 1e-2 since the last recomputation, and always before declaring
+//          convergence ("reliable updates").
+// Every reduction is two-stage (fixed per-CTA partials, then one CTA in fixed order), so
+// results are bitwise repeatable run to run.
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+#define RB MSTOPO_RED_BLOCKS
+#define RT 256
+
+// --------------------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    v = lane < (blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;   // valid in thread 0
+}
+
+template <typename A, typename B>
+__global__ void __launch_bounds__(RT) k_dot(const A* __restrict__ a, const B* __restrict__ b,
+                                            long long n, long long stride,
+                                            double* __restrict__ partials) {
+  __shared__ double sh[32];
+  a += blockIdx.y * stride;
+  b += blockIdx.y * stride;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
+    s = fma((double)a[i], (double)b[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.y * RB + blockIdx.x] = s;
+}
+
+__global__ void k_finish_sum(const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < RB; i += blockDim.x) s += partials[blockIdx.x * RB + i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+cudaError_t launch_dot_partials(const double* a, const double* b, long long n, int nsys,
+                                long long stride, double* partials, cudaStream_t s) {
+  k_dot<double, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_dot_partials_f32(const float* a, const float* b, long long n, int nsys,
+                                    long long stride, double* partials, cudaStream_t s) {
+  k_dot<float, float><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_dot_partials_mix(const float* a, const double* b, long long n, int nsys,
+                                    long long stride, double* partials, cudaStream_t s) {
+  k_dot<float, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_finish_sum(const double* partials, int nsys, double* out, cudaStream_t s) {
+  k_finish_sum<<<nsys, RT, 0, s>>>(partials, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------- conversions
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+// b = a with Dirichlet DOFs zeroed (a == NULL: b = 0)
+__global__ void k_mask_copy(const double* __restrict__ a, double* __restrict__ b,
+                            const uint8_t* __restrict__ m, long long n_nodes, long long stride) {
+  a = a ? a + blockIdx.y * stride : nullptr;
+  b += blockIdx.y * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint8_t f = m[i];
+    double2 v = a ? reinterpret_cast<const double2*>(a)[i] : make_double2(0.0, 0.0);
+    if (f & 1) v.x = 0.0;
+    if (f & 2) v.y = 0.0;
+    reinterpret_cast<double2*>(b)[i] = v;
+  }
+}
+
+cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t s) {
+  k_d2f<<<608, 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t s) {
+  k_f2d<<<608, 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_mask_copy(const double* a, double* b, const uint8_t* nmask, long long n_nodes,
+                             int nsys, long long stride, cudaStream_t s) {
+  k_mask_copy<<<dim3(304, nsys), 256, 0, s>>>(a, b, nmask, n_nodes, stride);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------- FCG steps
+// beta = -(z^T q_prev) / (p_prev^T q_prev); zero on the first step after a (re)start
+__global__ void k_scalar_beta(FcgScalars* sc, const double* __restrict__ zq, int restart) {
+  FcgScalars& c = sc[threadIdx.x];
+  if (!c.active) return;
+  c.zq = zq[threadIdx.x];
+  c.beta = restart ? 0.0 : -c.zq / c.pq_prev;
+}
+
+// p = z + beta p  (PT = float in MIXED mode, double in FP64 mode)
+template <typename PT>
+__global__ void __launch_bounds__(RT) k_pupdate(const PT* __restrict__ z, PT* __restrict__ p,
+                                                long long n, long long stride,
+                                                const FcgScalars* __restrict__ sc) {
+  const FcgScalars& c = sc[blockIdx.y];
+  if (!c.active) return;
+  z += blockIdx.y * stride;
+  p += blockIdx.y * stride;
+  const double beta = c.beta;
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
+    p[i] = (PT)((double)z[i] + beta * (double)p[i]);
+}
+
+// partial sums of p^T q and p^T r in one pass
+template <typename PT>
+__global__ void __launch_bounds__(RT) k_pq_pr(const PT* __restrict__ p, const PT* __restrict__ q,
+                                              const double* __restrict__ r, long long n,
+                                              long long stride, double* __restrict__ partials,
+                                              const FcgScalars* __restrict__ sc) {
+  __shared__ double sh[32];
+  if (!sc[blockIdx.y].active) return;
+  p += blockIdx.y * stride;
+  q += blockIdx.y * stride;
+  r += blockIdx.y * stride;
+  double s1 = 0.0, s2 = 0.0;
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT) {
+    double pv = (double)p[i];
+    s1 = fma(pv, (double)q[i], s1);
+    s2 = fma(pv, r[i], s2);
+  }
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    partials[(blockIdx.y * 2 + 0) * RB + blockIdx.x] = s1;
+    partials[(blockIdx.y * 2 + 1) * RB + blockIdx.x] = s2;
+  }
+}
+
+__global__ void k_scalar_alpha(FcgScalars* sc, const double* __restrict__ partials) {
+  __shared__ double sh[32];
+  FcgScalars& c = sc[blockIdx.x];
+  if (!c.active) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < RB; i += blockDim.x) {
+    s1 += partials[(blockIdx.x * 2 + 0) * RB + i];
+    s2 += partials[(blockIdx.x * 2 + 1) * RB + i];
+  }
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    c.pq = s1;
+    c.pr = s2;
+    if (!(s1 > 0.0) || !isfinite(s1) || !isfinite(s2)) {
+      c.status = isfinite(s1) && isfinite(s2) ? MSTOPO_NOT_SPD : MSTOPO_NONFINITE;
+      c.active = 0;
+      c.alpha = 0.0;
+    } else {
+      c.alpha = s2 / s1;
+      c.pq_prev = s1;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; (MIXED: r32 = float(r)) ; partial ||r||^2
+template <typename PT>
+__global__ void __launch_bounds__(RT) k_xr_update(double* __restrict__ x, double* __restrict__ r,
+                                                  float* __restrict__ r32,
+                                                  const PT* __restrict__ p,
+                                                  const PT* __restrict__ q, long long n,
+                                                  long long stride, double* __restrict__ partials,
+                                                  const FcgScalars* __restrict__ sc) {
+  __shared__ double sh[32];
+  if (!sc[blockIdx.y].active) return;
+  const double alpha = sc[blockIdx.y].alpha;
+  x += blockIdx.y * stride;
+  r += blockIdx.y * stride;
+  p += blockIdx.y * stride;
+  q += blockIdx.y * stride;
+  if (r32) r32 += blockIdx.y * stride;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT) {
+    x[i] = fma(alpha, (double)p[i], x[i]);
+    double rv = fma(-alpha, (double)q[i], r[i]);
+    r[i] = rv;
+    if (r32) r32[i] = (float)rv;
+    s = fma(rv, rv, s);
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.y * RB + blockIdx.x] = s;
+}
+
+__global__ void k_scalar_rr(FcgScalars* sc, const double* __restrict__ partials, double tol2) {
+  __shared__ double sh[32];
+  FcgScalars& c = sc[blockIdx.x];
+  if (!c.active) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < RB; i += blockDim.x) s += partials[blockIdx.x * RB + i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    c.rr = s;
+    c.iters += 1;
+    if (!isfinite(s)) {
+      c.status = MSTOPO_NONFINITE;
+      c.active = 0;
+    } else if (s <= tol2 * c.ff) {
+      c.active = 0;   // candidate: the host confirms with the true residual
+    }
+  }
+}
+
+// r = f - t (t = K x), r32 = float(r), partial ||r||^2
+__global__ void __launch_bounds__(RT) k_residual(const double* __restrict__ f,
+                                                 const double* __restrict__ t,
+                                                 double* __restrict__ r, float* __restrict__ r32,
+                                                 long long n, long long stride,
+                                                 double* __restrict__ partials) {
+  __shared__ double sh[32];
+  f += blockIdx.y * stride;
+  t += blockIdx.y * stride;
+  r += blockIdx.y * stride;
+  if (r32) r32 += blockIdx.y * stride;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT) {
+    double v = f[i] - t[i];
+    r[i] = v;
+    if (r32) r32[i] = (float)v;
+    s = fma(v, v, s);
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.y * RB + blockIdx.x] = s;
+}
+
+// --------------------------------------------------------------------------- host driver
+#define CK(x)                                                                   \
+  do {                                                                          \
+    cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                    \
+      h->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x;      \
+      return e_ == cudaErrorMemoryAllocation ? MSTOPO_OUT_OF_MEMORY : MSTOPO_CUDA_ERROR; \
+    }                                                                           \
+  } while (0)
+
+mstopo_status solver_alloc(mstopo_handle* h) {
+  Solver& sv = h->sv;
+  if (sv.x) return MSTOPO_OK;
+  sv.n = h->n_dof;
+  size_t nd = (size_t)MSTOPO_MAX_SYS * sv.n;
+  CK(cudaMalloc(&sv.x, nd * 8));
+  CK(cudaMalloc(&sv.r, nd * 8));
+  CK(cudaMalloc(&sv.f, nd * 8));
+  CK(cudaMalloc(&sv.tmp, nd * 8));
+  if (h->p.precision == MSTOPO_FP64) {
+    CK(cudaMalloc(&sv.p64, nd * 8));
+    CK(cudaMalloc(&sv.q64, nd * 8));
+    CK(cudaMalloc(&sv.z64, nd * 8));
+  } else {
+    CK(cudaMalloc(&sv.p32, nd * 4));
+    CK(cudaMalloc(&sv.q32, nd * 4));
+    CK(cudaMalloc(&sv.z32, nd * 4));
+    CK(cudaMalloc(&sv.r32, nd * 4));
+  }
+  CK(cudaMalloc(&sv.partials, (size_t)MSTOPO_MAX_SYS * 4 * RB * 8));
+  CK(cudaMalloc(&sv.sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
+  CK(cudaMallocHost(&sv.h_sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
+  return MSTOPO_OK;
+}
+
+void solver_free(Solver& sv) {
+  cudaFree(sv.x); cudaFree(sv.r); cudaFree(sv.f); cudaFree(sv.tmp);
+  cudaFree(sv.p64); cudaFree(sv.q64); cudaFree(sv.z64);
+  cudaFree(sv.p32); cudaFree(sv.q32); cudaFree(sv.z32); cudaFree(sv.r32);
+  cudaFree(sv.partials); cudaFree(sv.sc);
+  if (sv.h_sc) cudaFreeHost(sv.h_sc);
+  sv = Solver();
+}
+
+// FP64 true residual for all systems: r = f - K64(E_k) x ; rr_out[s] = ||r||^2
+static mstopo_status true_residual(mstopo_handle* h, int sys0, int nsys, double* rr_dev) {
+  Solver& sv = h->sv;
+  const long long n = sv.n;
+  CK(launch_matvec_f64(sv.x, sv.tmp, h->d_E64 + (long long)sys0 * h->n_el, h->d_nmask, h->nelx,
+                       h->nely, h->st64, nsys, n, h->n_el, h->s));
+  k_residual<<<dim3(RB, nsys), RT, 0, h->s>>>(sv.f, sv.tmp, sv.r, sv.r32, n, n, sv.partials);
+  CK(cudaGetLastError());
+  CK(launch_finish_sum(sv.partials, nsys, rr_dev, h->s));
+  return MSTOPO_OK;
+}
+
+__global__ void k_set_rr(FcgScalars* sc, const double* __restrict__ v, int which, double tol2) {
+  FcgScalars& c = sc[threadIdx.x];
+  if (which == 0) c.ff = v[threadIdx.x];
+  else c.rr = v[threadIdx.x];
+  if (which == 1) c.active = (c.rr > tol2 * c.ff) ? 1 : 0;
+}
+
+static mstopo_status precond(mstopo_handle* h, int nsys) {
+  Solver& sv = h->sv;
+  cudaError_t e;
+  if (h->p.precision == MSTOPO_FP64) e = precond_apply_f64(h, sv.r, sv.z64, nsys, 0);
+  else e = precond_apply_f32(h, sv.r32, sv.z32, nsys, 0);
+  CK(e);
+  return MSTOPO_OK;
+}
+
+mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
+                        const double* u0, mstopo_solve_info* infos) {
+  Solver& sv = h->sv;
+  const long long n = sv.n;
+  const bool mixed = h->p.precision != MSTOPO_FP64;
+  const double tol2 = h->p.tol * h->p.tol;
+  mstopo_status st = solver_alloc(h);
+  if (st != MSTOPO_OK) return st;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, h->s));
+  // f (same load for every system), masked; x0
+  for (int s = 0; s < nsys; ++s) CK(launch_mask_copy(f, sv.f + s * n, h->d_nmask, h->n_nodes, 1, n, h->s));
+  CK(launch_mask_copy(u0, sv.x, h->d_nmask, h->n_nodes, nsys, n, h->s));
+  FcgScalars init;
+  memset(&init, 0, sizeof(init));
+  init.active = 1;
+  init.status = MSTOPO_OK;
+  for (int s = 0; s < nsys; ++s) sv.h_sc[s] = init;
+  CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
+  double* vtmp = sv.partials + (size_t)MSTOPO_MAX_SYS * 3 * RB;   // small scratch [nsys]
+  CK(launch_dot_partials(sv.f, sv.f, n, nsys, n, sv.partials, h->s));
+  CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+  k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 0, tol2);
+  CK(cudaGetLastError());
+  st = true_residual(h, sys0, nsys, vtmp);
+  if (st != MSTOPO_OK) return st;
+  k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 1, tol2);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  double rr_last[MSTOPO_MAX_SYS];
+  int done[MSTOPO_MAX_SYS] = {0}, repl[MSTOPO_MAX_SYS] = {0}, restart = 1;
+  for (int s = 0; s < nsys; ++s) {
+    rr_last[s] = sv.h_sc[s].rr;
+    if (sv.h_sc[s].ff == 0.0) {
+      h->err = "zero load vector";
+      return MSTOPO_INVALID_ARG;
+    }
+    if (!sv.h_sc[s].active) done[s] = 1;
+  }
+  const float* E32 = h->d_E32 + (long long)sys0 * h->n_el;
+  const double* E64 = h->d_E64 + (long long)sys0 * h->n_el;
+  const int chunk = 4;
+  int total_iters = 0;
+  while (true) {
+    int n_active = 0;
+    for (int s = 0; s < nsys; ++s) n_active += !done[s];
+    if (n_active == 0) break;
+    for (int it = 0; it < chunk; ++it) {
+      st = precond(h, nsys);
+      if (st != MSTOPO_OK) return st;
+      if (!restart) {
+        if (mixed) CK(launch_dot_partials_f32(sv.z32, sv.q32, n, nsys, n, sv.partials, h->s));
+        else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));
+        CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+      }
+      k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, restart);
+      CK(cudaGetLastError());
+      restart = 0;
+      if (mixed) {
+        k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
+        CK(cudaGetLastError());
+        CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
+                             h->n_el, h->s));
+        k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
+      } else {
+        k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
+        CK(cudaGetLastError());
+        CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
+                             h->n_el, h->s));
+        k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
+      }
+      CK(cudaGetLastError());
+      k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
+      CK(cudaGetLastError());
+      if (mixed)
+        k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
+                                                            sv.partials, sv.sc);
+      else
+        k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
+                                                             n, sv.partials, sv.sc);
+      CK(cudaGetLastError());
+      k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
+      CK(cudaGetLastError());
+    }
+    total_iters += chunk;
+    CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    // host decisions: convergence candidates and reliable updates need the true residual
+    bool need_true = false;
+    for (int s = 0; s < nsys; ++s) {
+      if (done[s]) continue;
+      FcgScalars& c = sv.h_sc[s];
+      if (c.status != MSTOPO_OK) { done[s] = 1; continue; }
+      if (!c.active) need_true = true;
+      else if (mixed && c.rr < 1e-4 * rr_last[s]) need_true = true;
+      if (c.iters >= h->p.max_iter) { c.status = MSTOPO_MAX_ITER; done[s] = 1; }
+    }
+    if (need_true) {
+      st = true_residual(h, sys0, nsys, vtmp);
+      if (st != MSTOPO_OK) return st;
+      double rr_true[MSTOPO_MAX_SYS];
+      CK(cudaMemcpyAsync(rr_true, vtmp, nsys * 8, cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      for (int s = 0; s < nsys; ++s) {
+        FcgScalars& c = sv.h_sc[s];
+        repl[s]++;
+        c.rr = rr_true[s];
+        rr_last[s] = rr_true[s];
+        if (done[s]) { c.active = 0; continue; }
+        if (rr_true[s] <= tol2 * c.ff) { c.active = 0; done[s] = 1; }
+        else c.active = 1;
+      }
+      // the true residual replaced r for every system (finished ones are unchanged in x)
+      CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
+    } else {
+      for (int s = 0; s < nsys; ++s) if (done[s] && sv.h_sc[s].active) sv.h_sc[s].active = 0;
+      CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
+    }
+    if (total_iters > h->p.max_iter + chunk) break;
+  }
+  CK(cudaEventRecord(ev1, h->s));
+  // outputs
+  CK(cudaMemcpyAsync(u, sv.x, (size_t)nsys * n * 8, cudaMemcpyDeviceToDevice, h->s));
+  // compliance f^T u
+  CK(launch_dot_partials(sv.f, sv.x, n, nsys, n, sv.partials, h->s));
+  CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+  double comp[MSTOPO_MAX_SYS];
+  CK(cudaMemcpyAsync(comp, vtmp, nsys * 8, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  mstopo_status worst = MSTOPO_OK;
+  for (int s = 0; s < nsys; ++s) {
+    const FcgScalars& c = sv.h_sc[s];
+    if (c.status != MSTOPO_OK && worst == MSTOPO_OK) worst = (mstopo_status)c.status;
+    if (infos) {
+      infos[s].status = c.status;
+      infos[s].iterations = c.iters;
+      infos[s].replacements = repl[s];
+      infos[s].rel_residual = std::sqrt(c.rr / c.ff);
+      infos[s].compliance = comp[s];
+      infos[s].ms = ms;
+    }
+  }
+  if (worst != MSTOPO_OK) h->err = "flexible CG did not converge (see per-system status)";
+  return worst;
+}

@@ -1,0 +1,1041 @@
+// Two-level preconditioner with a spectral MsFEM coarse space (paper Sec. 2.4, 2.4.1,
+// 2.4.2, 3.2, 5.3).
+//
+// Build (once per design):
+//   1. agglomerate de-duplication (Sec. 2.4.1): every agglomerate omega_i (the 2H x 2H
+//      elements around coarse node y_i, clipped by the mesh) is hashed over its moduli and
+//      its Dirichlet mask; agglomerates with equal hashes share one "type" and therefore one
+//      eigenbasis and one patch factor.  The paper observes three unique agglomerates for a
+//      periodic double-clamped beam; the hash generalises that to any design.
+//   2. per type, the agglomerate's Neumann matrix K_w (its own elements only, physical
+//      Dirichlet DOFs kept) is assembled block-tridiagonally by node rows; K_w + s diag(K_w)
+//      is factorised (FP64) and block subspace iteration with Rayleigh-Ritz finds the
+//      smallest eigenpairs of K_w psi = lambda diag(K_w) psi (Sec. 2.4 and the diagonal
+//      weighting of Sec. 3.2), psi^T diag(K_w) psi = 1.  Either n_eig pairs or those below
+//      lambda_Omega (capped) are kept.
+//   3. the coarse basis phi_ij = chi_i psi_j with chi_i the bilinear hat of y_i (a partition
+//      of unity with |grad chi| <= 1/H); K_c = R_c K R_c^T (Eq. coarse_projection) is
+//      assembled element by element for each pair of overlapping agglomerates (3x3 coarse
+//      neighbours), factorised block-tridiagonally by coarse-node lines in FP64, and
+//      inverted explicitly (dense FP64) for a one-GEMV coarse solve.
+//   4. per type, the overlapping patch matrix K_i = K restricted to the nodes of omega_i off
+//      its artificial boundary (zero Dirichlet there, physical conditions kept) is factorised
+//      block-tridiagonally (FP64, plus an FP32 copy for the MIXED solver).
+// Apply (every Krylov iteration): z = R_c^T K_c^-1 R_c r + sum_i R_i^T K_i^-1 R_i r
+// (two-level additive Schwarz, cited in Sec. 2.4.2), with deterministic gathers (no atomics).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "blocktri.cuh"
+
+#define PC_THREADS 256
+#define PC_GROUP 4          // patches of one type solved together per CTA (x systems)
+#define EIG_MAX_SWEEPS 80
+#define EIG_TOL 1e-7
+#define EIG_SHIFT 1e-5
+
+struct K0P { double k[64]; };
+
+// ------------------------------------------------------------------------------ hashing
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restrict__ nmask,
+                           int nelx, int nely, int H, int ncx,
+                           unsigned long long* __restrict__ hash) {
+  const int i = blockIdx.x;
+  const int I = i % (ncx + 1), J = i / (ncx + 1);
+  const int ox = (I - 1) * H, oy = (J - 1) * H;
+  const int ne = 2 * H, nn = 2 * H + 1;
+  unsigned long long h1 = 0, h2 = 0;
+  for (int t = threadIdx.x; t < ne * ne; t += blockDim.x) {
+    int ex = ox + t % ne, ey = oy + t / ne;
+    unsigned long long v = 0xFFFFFFFFFFFFFFFFull;
+    if (ex >= 0 && ex < nelx && ey >= 0 && ey < nely)
+      v = (unsigned long long)__double_as_longlong(E[(long long)ey * nelx + ex]);
+    h1 ^= mix64(v ^ mix64((unsigned long long)t * 2 + 1));
+    h2 ^= mix64(v * 0xD6E8FEB86659FD93ull + mix64((unsigned long long)t + 0x1234567ull));
+  }
+  for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
+    int x = ox + t % nn, y = oy + t / nn;
+    unsigned long long v = 7;
+    if (x >= 0 && x <= nelx && y >= 0 && y <= nely) v = nmask[(long long)y * (nelx + 1) + x];
+    h1 ^= mix64((v + 11) ^ mix64(((unsigned long long)t << 20) + 3));
+    h2 ^= mix64((v + 101) * 0x9E3779B97F4A7C15ull ^ ((unsigned long long)t << 7));
+  }
+  atomicXor(&hash[2 * i], h1);
+  atomicXor(&hash[2 * i + 1], h2);
+}
+
+// ----------------------------------------------------------------------------- assembly
+// Block-tridiagonal assembly of a box operator.  Box node (a, b), a, b in [0, N), is global
+// node (ox + a, oy + b); line = b, DOF in line = 2a + c.  Only elements with
+// ex in [ex0, ex1), ey in [ey0, ey1) and inside the mesh contribute.  A DOF is free when its
+// node is in the mesh and not Dirichlet; other rows/columns are identity.
+struct BoxSpec { int ox, oy, N, ex0, ex1, ey0, ey1; };
+
+__global__ void k_assemble_box(const double* __restrict__ E, const uint8_t* __restrict__ nmask,
+                               int nelx, int nely, const int* __restrict__ rep, int H, int ncx,
+                               int off, int elem_lo, int elem_hi, K0P K0, double* __restrict__ A,
+                               double* __restrict__ B, uint8_t* __restrict__ freeo) {
+  // blockIdx.x = type, blockIdx.y = line
+  const int type = blockIdx.x, line = blockIdx.y;
+  const int ia = rep[type];
+  const int I = ia % (ncx + 1), J = ia / (ncx + 1);
+  const int N = 2 * H + 1 - 2 * off;
+  const int ox = (I - 1) * H + off, oy = (J - 1) * H + off;
+  // element window: [ (I-1)H + elem_lo, (I+1)H + elem_hi )
+  const int ex0 = (I - 1) * H + elem_lo, ex1 = (I + 1) * H + elem_hi;
+  const int ey0 = (J - 1) * H + elem_lo, ey1 = (J + 1) * H + elem_hi;
+  const int nb = 2 * N;
+  const long long nn = (long long)nb * nb;
+  double* Ak = A + ((long long)type * N + line) * nn;
+  double* Bk = line > 0 ? B + ((long long)type * (N - 1) + line - 1) * nn : nullptr;
+  auto dof_free = [&](int a, int b, int c) -> bool {
+    int x = ox + a, y = oy + b;
+    if (a < 0 || a >= N || b < 0 || b >= N) return false;
+    if (x < 0 || x > nelx || y < 0 || y > nely) return false;
+    return !((nmask[(long long)y * (nelx + 1) + x] >> c) & 1);
+  };
+  for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+    for (int c = 0; c < nb; ++c) {
+      Ak[(long long)r * nb + c] = 0.0;
+      if (Bk) Bk[(long long)r * nb + c] = 0.0;
+    }
+    const int a = r >> 1, cr = r & 1;
+    const bool rf = dof_free(a, line, cr);
+    freeo[((long long)type * N + line) * nb + r] = rf ? 1 : 0;
+    if (!rf) {
+      Ak[(long long)r * nb + r] = 1.0;
+      continue;
+    }
+    const int gx = ox + a, gy = oy + line;
+    // the four elements around the node; local node order (0,0),(1,0),(1,1),(0,1)
+    for (int q = 0; q < 4; ++q) {
+      const int ex = gx - 1 + (q & 1), ey = gy - 1 + (q >> 1);
+      if (ex < ex0 || ex >= ex1 || ey < ey0 || ey >= ey1) continue;
+      if (ex < 0 || ex >= nelx || ey < 0 || ey >= nely) continue;
+      const double Ee = E[(long long)ey * nelx + ex];
+      const int lx = gx - ex, ly = gy - ey;   // node position inside the element
+      const int la = ly == 0 ? (lx == 0 ? 0 : 1) : (lx == 1 ? 2 : 3);
+      for (int lb = 0; lb < 4; ++lb) {
+        const int mx = ex + ((lb == 1 || lb == 2) ? 1 : 0), my = ey + (lb >= 2 ? 1 : 0);
+        const int ma = mx - ox, mb = my - oy;
+        for (int cc = 0; cc < 2; ++cc) {
+          if (!dof_free(ma, mb, cc)) continue;
+          const double v = Ee * K0.k[(2 * la + cr) * 8 + 2 * lb + cc];
+          const int col = 2 * ma + cc;
+          if (mb == line) Ak[(long long)r * nb + col] += v;
+          else if (mb == line - 1) Bk[(long long)r * nb + col] += v;
+          // mb == line + 1 belongs to A(line, line+1) = B_line^T, written by the next line
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ factorisation
+__global__ void k_bt_factor(const double* __restrict__ A, const double* __restrict__ B,
+                            const uint8_t* __restrict__ freem, double shift, int nb, int NL,
+                            double* __restrict__ Linv, double* __restrict__ C,
+                            double* __restrict__ Swork, int* __restrict__ status) {
+  __shared__ int sh_fail;
+  const long long nn = (long long)nb * nb;
+  const int sys = blockIdx.x;
+  int f = bt_factor(A + sys * NL * nn, B + sys * (NL - 1) * nn,
+                    freem ? freem + (long long)sys * NL * nb : nullptr, shift, nb, NL,
+                    Linv + sys * NL * nn, C + sys * (NL - 1) * nn, Swork + sys * nn, &sh_fail);
+  if (threadIdx.x == 0) status[sys] = f;
+}
+
+__global__ void k_d2f_copy(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------------------ eigen
+// Small dense helpers (thread 0 only).  Cyclic Jacobi for a symmetric q x q matrix:
+// on exit A is (numerically) diagonal and V holds the eigenvectors as columns.
+__device__ void jacobi_eig(double* A, double* V, int q) {
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) V[i * q + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        double v = A[i * q + j] * A[i * q + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < q - 1; ++p)
+      for (int r = p + 1; r < q; ++r) {
+        double apr = A[p * q + r];
+        if (fabs(apr) < 1e-300) continue;
+        double app = A[p * q + p], arr = A[r * q + r];
+        double theta = (arr - app) / (2.0 * apr);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < q; ++k) {   // columns p, r
+          double akp = A[k * q + p], akr = A[k * q + r];
+          A[k * q + p] = c * akp - s * akr;
+          A[k * q + r] = s * akp + c * akr;
+        }
+        for (int k = 0; k < q; ++k) {   // rows p, r
+          double apk = A[p * q + k], ark = A[r * q + k];
+          A[p * q + k] = c * apk - s * ark;
+          A[r * q + k] = s * apk + c * ark;
+        }
+        for (int k = 0; k < q; ++k) {
+          double vkp = V[k * q + p], vkr = V[k * q + r];
+          V[k * q + p] = c * vkp - s * vkr;
+          V[k * q + r] = s * vkp + c * vkr;
+        }
+      }
+  }
+}
+
+// Rayleigh-Ritz on (G, M) (q x q, symmetric, M SPD): theta ascending, W (q x q) with
+// W^T M W = I and W^T G W = diag(theta).  Uses scratch of 3 q^2 doubles.  Thread 0 only.
+__device__ int rayleigh_ritz(double* G, double* M, int q, double* theta, double* W, double* s) {
+  double* L = s;             // chol(M)
+  double* T = s + q * q;     // L^-1 G L^-T
+  double* V = s + 2 * q * q;
+  for (int i = 0; i < q * q; ++i) L[i] = 0.0;
+  for (int j = 0; j < q; ++j) {
+    double d = M[j * q + j];
+    for (int k = 0; k < j; ++k) d -= L[j * q + k] * L[j * q + k];
+    if (!(d > 0.0)) return 1;
+    d = sqrt(d);
+    L[j * q + j] = d;
+    for (int i = j + 1; i < q; ++i) {
+      double v = M[i * q + j];
+      for (int k = 0; k < j; ++k) v -= L[i * q + k] * L[j * q + k];
+      L[i * q + j] = v / d;
+    }
+  }
+  // Linv in V (temporarily)
+  for (int c = 0; c < q; ++c)
+    for (int i = 0; i < q; ++i) {
+      if (i < c) { V[i * q + c] = 0.0; continue; }
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int l = c; l < i; ++l) v -= L[i * q + l] * V[l * q + c];
+      V[i * q + c] = v / L[i * q + i];
+    }
+  // T = Linv G Linv^T, as two products (W holds Linv G)
+  for (int i = 0; i < q; ++i)
+    for (int b = 0; b < q; ++b) {
+      double v = 0.0;
+      for (int a = 0; a <= i; ++a) v += V[i * q + a] * G[a * q + b];
+      W[i * q + b] = v;
+    }
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      double v = 0.0;
+      for (int b = 0; b <= j; ++b) v += W[i * q + b] * V[j * q + b];
+      T[i * q + j] = v;
+    }
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < i; ++j) {
+      double v = 0.5 * (T[i * q + j] + T[j * q + i]);
+      T[i * q + j] = T[j * q + i] = v;
+    }
+  // keep Linv: copy into L's storage
+  for (int i = 0; i < q * q; ++i) L[i] = V[i];
+  jacobi_eig(T, V, q);
+  // sort ascending
+  int idx[MSTOPO_MAX_EIG * 2];
+  for (int i = 0; i < q; ++i) idx[i] = i;
+  for (int i = 1; i < q; ++i) {
+    int v = idx[i], j = i - 1;
+    while (j >= 0 && T[idx[j] * q + idx[j]] > T[v * q + v]) { idx[j + 1] = idx[j]; --j; }
+    idx[j + 1] = v;
+  }
+  // W = Linv^T V(:, idx)
+  for (int j = 0; j < q; ++j) {
+    theta[j] = T[idx[j] * q + idx[j]];
+    for (int i = 0; i < q; ++i) {
+      double v = 0.0;
+      for (int a = i; a < q; ++a) v += L[a * q + i] * V[a * q + idx[j]];
+      W[i * q + j] = v;
+    }
+  }
+  return 0;
+}
+
+struct EigArgs {
+  const double* E; const uint8_t* nmask; int nelx, nely, H, ncx;
+  const int* rep; const double* A; const uint8_t* freem;
+  const double* Linv; const double* C;     // factor of K_w + shift diag(K_w)
+  double* X; double* Y; double* KY;        // [T][NL][nb][q]
+  int q, kmax; double lam_thresh;
+  double* lambda; int* kept; double* res; int* sweeps;
+  K0P K0;
+};
+
+// y = K_w x on the agglomerate box (elements of the agglomerate only), R columns,
+// [N][nb][R] layout; zero on non-free DOFs.
+__device__ void box_apply(const EigArgs& a, int I, int J, const uint8_t* freem, const double* x,
+                          double* y, int R) {
+  const int H = a.H, N = 2 * H + 1, nb = 2 * N;
+  const int ox = (I - 1) * H, oy = (J - 1) * H;
+  for (int t = threadIdx.x; t < N * nb * R; t += blockDim.x) {
+    const int r = t % R, dof = t / R;
+    const int line = dof / nb, rr = dof % nb, na = rr >> 1, cr = rr & 1;
+    double s = 0.0;
+    if (freem[dof]) {
+      const int gx = ox + na, gy = oy + line;
+      for (int q = 0; q < 4; ++q) {
+        const int ex = gx - 1 + (q & 1), ey = gy - 1 + (q >> 1);
+        if (ex < ox || ex >= ox + 2 * H || ey < oy || ey >= oy + 2 * H) continue;
+        if (ex < 0 || ex >= a.nelx || ey < 0 || ey >= a.nely) continue;
+        const double Ee = a.E[(long long)ey * a.nelx + ex];
+        const int lx = gx - ex, ly = gy - ey;
+        const int la = ly == 0 ? (lx == 0 ? 0 : 1) : (lx == 1 ? 2 : 3);
+        double es = 0.0;
+        for (int lb = 0; lb < 4; ++lb) {
+          const int mx = ex + ((lb == 1 || lb == 2) ? 1 : 0) - ox, my = ey + (lb >= 2 ? 1 : 0) - oy;
+          const long long md = (long long)my * nb + 2 * mx;
+          es = fma(a.K0.k[(2 * la + cr) * 8 + 2 * lb], x[md * R + r], es);
+          es = fma(a.K0.k[(2 * la + cr) * 8 + 2 * lb + 1], x[(md + 1) * R + r], es);
+        }
+        s = fma(Ee, es, s);
+      }
+    }
+    y[t] = s;
+  }
+}
+
+__global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
+  extern __shared__ double smem[];
+  const int type = blockIdx.x;
+  const int H = a.H, N = 2 * H + 1, nb = 2 * N, q = a.q;
+  const long long n = (long long)N * nb, nn = (long long)nb * nb;
+  const int ia = a.rep[type];
+  const int I = ia % (a.ncx + 1), J = ia / (a.ncx + 1);
+  const double* Ak = a.A + (long long)type * N * nn;
+  const uint8_t* fr = a.freem + (long long)type * n;
+  const double* Linv = a.Linv + (long long)type * N * nn;
+  const double* C = a.C + (long long)type * (N - 1) * nn;
+  double* X = a.X + (long long)type * n * q;
+  double* Y = a.Y + (long long)type * n * q;
+  double* KY = a.KY + (long long)type * n * q;
+  double* stage = smem;                    // nn
+  double* t0 = stage + nn;                 // nb*q
+  double* t1 = t0 + nb * q;                // nb*q
+  double* G = t1 + nb * q;                 // q*q
+  double* M = G + q * q;                   // q*q
+  double* W = M + q * q;                   // q*q
+  double* scr = W + q * q;                 // 3 q*q
+  double* theta = scr + 3 * q * q;         // q
+  double* res = theta + q;                 // q
+  __shared__ int s_done, s_fail;
+  // D = diag(K_w) per DOF (from the assembled diagonal blocks)
+  auto Dof = [&](long long dof) -> double {
+    long long line = dof / nb, r = dof % nb;
+    return Ak[line * nn + r * nb + r];
+  };
+  // deterministic start block, zero on non-free DOFs
+  for (long long t = threadIdx.x; t < n * q; t += blockDim.x) {
+    long long dof = t / q;
+    unsigned long long z = mix64((unsigned long long)t * 0x9E3779B97F4A7C15ull + 12345u);
+    X[t] = fr[dof] ? ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5) : 0.0;
+  }
+  if (threadIdx.x == 0) { s_done = 0; s_fail = 0; }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < EIG_MAX_SWEEPS && !s_done; ++sweep) {
+    // Y = (K + s D)^-1 D X
+    for (long long t = threadIdx.x; t < n * q; t += blockDim.x) Y[t] = Dof(t / q) * X[t] * fr[t / q];
+    __syncthreads();
+    bt_solve<double, true>(Linv, C, nb, N, Y, q, stage, t0, t1);
+    for (long long t = threadIdx.x; t < n * q; t += blockDim.x) if (!fr[t / q]) Y[t] = 0.0;
+    __syncthreads();
+    box_apply(a, I, J, fr, Y, KY, q);
+    __syncthreads();
+    // G = Y^T K Y, M = Y^T D Y
+    for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+      int i = t / q, j = t % q;
+      double g = 0.0, m = 0.0;
+      for (long long d = 0; d < n; ++d) {
+        double yi = Y[d * q + i];
+        g = fma(yi, KY[d * q + j], g);
+        m = fma(yi * Dof(d), Y[d * q + j], m);
+      }
+      G[t] = g;
+      M[t] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < q; ++i)
+        for (int j = 0; j < i; ++j) {
+          double g = 0.5 * (G[i * q + j] + G[j * q + i]), m = 0.5 * (M[i * q + j] + M[j * q + i]);
+          G[i * q + j] = G[j * q + i] = g;
+          M[i * q + j] = M[j * q + i] = m;
+        }
+      if (rayleigh_ritz(G, M, q, theta, W, scr)) s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) break;
+    // X = Y W, KX (in KY) = KY W, row by row
+    for (long long d = threadIdx.x; d < n; d += blockDim.x) {
+      double yr[2 * MSTOPO_MAX_EIG], kr[2 * MSTOPO_MAX_EIG];
+      for (int i = 0; i < q; ++i) { yr[i] = Y[d * q + i]; kr[i] = KY[d * q + i]; }
+      for (int j = 0; j < q; ++j) {
+        double xs = 0.0, ks = 0.0;
+        for (int i = 0; i < q; ++i) { xs = fma(yr[i], W[i * q + j], xs); ks = fma(kr[i], W[i * q + j], ks); }
+        X[d * q + j] = xs;
+        KY[d * q + j] = ks;
+      }
+    }
+    __syncthreads();
+    // residual norms of the wanted pairs: ||K x - theta D x||_{D^-1}
+    const int kw = a.kmax;
+    for (int j = threadIdx.x; j < kw; j += blockDim.x) {
+      double s = 0.0;
+      for (long long d = 0; d < n; ++d) {
+        if (!fr[d]) continue;
+        double Dd = Dof(d);
+        double v = KY[d * q + j] - theta[j] * Dd * X[d * q + j];
+        s = fma(v, v / Dd, s);
+      }
+      res[j] = sqrt(s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int j = 0; j < kw; ++j) m = fmax(m, res[j]);
+      if (m <= EIG_TOL) s_done = 1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int kept = a.kmax;
+    if (a.lam_thresh > 0.0) {
+      kept = 0;
+      while (kept < a.kmax && theta[kept] < a.lam_thresh) ++kept;
+      if (kept < 1) kept = 1;
+    }
+    double m = 0.0;
+    for (int j = 0; j < a.kmax; ++j) {
+      a.lambda[type * MSTOPO_MAX_EIG + j] = theta[j];
+      if (j < kept) m = fmax(m, res[j]);
+    }
+    a.kept[type] = s_fail ? -1 : kept;
+    a.res[type] = m;
+    a.sweeps[type] = sweep;
+  }
+}
+
+// Psi[type][node][c][j] from X[type][dof][q] (dof = node*2 + c), zero for j >= kept
+__global__ void k_store_psi(const double* __restrict__ X, const int* __restrict__ kept, int n,
+                            int q, int kmax, double* __restrict__ psi64, float* __restrict__ psi32) {
+  const int type = blockIdx.y;
+  const int k = kept[type];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * kmax;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long dof = t / kmax;
+    int j = t % kmax;
+    double v = j < k ? X[((long long)type * n + dof) * q + j] : 0.0;
+    psi64[(long long)type * n * kmax + t] = v;
+    psi32[(long long)type * n * kmax + t] = (float)v;
+  }
+}
+
+// ------------------------------------------------------------------- coarse assembly
+// Coarse unknowns are ordered agglomerate by agglomerate (i = J*(ncx+1) + I), offsets coff.
+// For the block-tridiagonal factorisation they are grouped in lines of coarse nodes along
+// the shorter coarse dimension: line L, position p in the line, slot p*kmax + a.
+struct CoarseMap { int by_columns; int ncx, ncy, kmax; };
+
+__device__ __forceinline__ void coarse_line_pos(const CoarseMap& m, int I, int J, int& line, int& pos) {
+  if (m.by_columns) { line = I; pos = J; } else { line = J; pos = I; }
+}
+
+__device__ __forceinline__ double hat(int x, int c, int H) {
+  double d = fabs((double)(x - c)) / H;
+  return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+__global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
+    const double* __restrict__ E, int nelx, int nely, int H, const int* __restrict__ type_of,
+    const int* __restrict__ kept, const double* __restrict__ psi, int kmax, K0P K0, CoarseMap cm,
+    double* __restrict__ Ac, double* __restrict__ Bc, int nbc) {
+  // blockIdx.x = agglomerate i, blockIdx.y = neighbour (dI, dJ) in [-1,1]^2
+  __shared__ double red[PC_THREADS / MSTOPO_MAX_EIG][MSTOPO_MAX_EIG][MSTOPO_MAX_EIG + 1];
+  const int ncx = cm.ncx, ncy = cm.ncy;
+  const int i = blockIdx.x;
+  const int I = i % (ncx + 1), J = i / (ncx + 1);
+  const int I2 = I + (int)blockIdx.y % 3 - 1, J2 = J + (int)blockIdx.y / 3 - 1;
+  if (I2 < 0 || I2 > ncx || J2 < 0 || J2 > ncy) return;
+  int L1, P1, L2, P2;
+  coarse_line_pos(cm, I, J, L1, P1);
+  coarse_line_pos(cm, I2, J2, L2, P2);
+  if (L2 == L1 - 1) return;   // stored through the transpose (block of line L2)
+  const int i2 = J2 * (ncx + 1) + I2;
+  const int t1 = type_of[i], t2 = type_of[i2];
+  const int k1 = kept[t1], k2 = kept[t2];
+  const int N = 2 * H + 1;
+  const long long n = (long long)N * N * 2;
+  const double* P1s = psi + (long long)t1 * n * kmax;
+  const double* P2s = psi + (long long)t2 * n * kmax;
+  // element overlap of the two agglomerates, inside the mesh
+  const int x0 = max(max((I - 1) * H, (I2 - 1) * H), 0), x1 = min(min((I + 1) * H, (I2 + 1) * H), nelx);
+  const int y0 = max(max((J - 1) * H, (J2 - 1) * H), 0), y1 = min(min((J + 1) * H, (J2 + 1) * H), nely);
+  const int lanes = PC_THREADS / MSTOPO_MAX_EIG;     // element lanes
+  const int b = threadIdx.x % MSTOPO_MAX_EIG, lane = threadIdx.x / MSTOPO_MAX_EIG;
+  double acc[MSTOPO_MAX_EIG];
+  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) acc[a] = 0.0;
+  const int nex = x1 - x0, ney = y1 - y0;
+  if (b < k2 && nex > 0 && ney > 0) {
+    for (int e = lane; e < nex * ney; e += lanes) {
+      const int ex = x0 + e % nex, ey = y0 + e / nex;
+      const double Ee = E[(long long)ey * nelx + ex];
+      double f2[8];                   // phi_2 (column b) at the element DOFs
+      double c1[4];                   // chi_1 at the element nodes
+      long long l1[4];                // node index in agglomerate 1's box
+#pragma unroll
+      for (int ln = 0; ln < 4; ++ln) {
+        const int nx = ex + ((ln == 1 || ln == 2) ? 1 : 0), ny = ey + (ln >= 2 ? 1 : 0);
+        c1[ln] = hat(nx, I * H, H) * hat(ny, J * H, H);
+        const double c2 = hat(nx, I2 * H, H) * hat(ny, J2 * H, H);
+        l1[ln] = (long long)(ny - (J - 1) * H) * N + (nx - (I - 1) * H);
+        const long long l2 = (long long)(ny - (J2 - 1) * H) * N + (nx - (I2 - 1) * H);
+        f2[2 * ln] = c2 * P2s[(l2 * 2) * kmax + b];
+        f2[2 * ln + 1] = c2 * P2s[(l2 * 2 + 1) * kmax + b];
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        double sdot = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sdot = fma(K0.k[rr * 8 + c], f2[c], sdot);
+        const double w = Ee * sdot * c1[rr >> 1];
+        const double* p1 = P1s + (l1[rr >> 1] * 2 + (rr & 1)) * kmax;
+        for (int a = 0; a < k1; ++a) acc[a] = fma(w, p1[a], acc[a]);
+      }
+    }
+  }
+  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) red[lane][b][a] = acc[a];
+  __syncthreads();
+  // reduce over lanes in fixed order and write the block
+  const int nn = nbc;
+  for (int t = threadIdx.x; t < MSTOPO_MAX_EIG * MSTOPO_MAX_EIG; t += blockDim.x) {
+    const int bb = t / MSTOPO_MAX_EIG, aa = t % MSTOPO_MAX_EIG;
+    if (aa >= kmax || bb >= kmax) continue;
+    double s = 0.0;
+    for (int l = 0; l < lanes; ++l) s += red[l][bb][aa];
+    const int row_slot = P1 * kmax + aa, col_slot = P2 * kmax + bb;
+    double v;
+    if (aa < k1 && bb < k2) v = s;
+    else v = (i == i2 && aa == bb) ? 1.0 : 0.0;   // padding slots: identity
+    if (L2 == L1) Ac[((long long)L1 * nn + row_slot) * nn + col_slot] = v;
+    else Bc[((long long)L1 * nn + col_slot) * nn + row_slot] = v;   // B_L1 = A(L1+1, L1)
+  }
+}
+
+// dense inverse of the coarse matrix: solve with identity right-hand sides, RC columns
+// (in line order) per CTA, scatter into Kcinv in the agglomerate order
+#define RC 16
+__global__ void __launch_bounds__(PC_THREADS) k_coarse_inverse(
+    const double* __restrict__ Linv, const double* __restrict__ C, int nbc, int NLc,
+    const int* __restrict__ slot2orig, int Nt, double* __restrict__ Xw, double* __restrict__ Kcinv) {
+  extern __shared__ double smem[];
+  double* t0 = smem;
+  double* t1 = t0 + nbc * RC;
+  const long long ntot = (long long)nbc * NLc;
+  const long long j0 = (long long)blockIdx.x * RC;
+  double* X = Xw + (long long)blockIdx.x * ntot * RC;
+  for (long long t = threadIdx.x; t < ntot * RC; t += blockDim.x) {
+    long long row = t / RC, r = t % RC;
+    X[t] = (row == j0 + r) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  bt_solve<double, false>(Linv, C, nbc, NLc, X, RC, nullptr, t0, t1);
+  for (long long t = threadIdx.x; t < ntot * RC; t += blockDim.x) {
+    long long row = t / RC, r = t % RC;
+    long long col = j0 + r;
+    if (col >= ntot) continue;
+    int orow = slot2orig[row], ocol = slot2orig[col];
+    if (orow < 0 || ocol < 0) continue;
+    Kcinv[(long long)orow * Nt + ocol] = X[t];
+  }
+}
+
+// ------------------------------------------------------------------------------ apply
+// rc[s][coff[i] + a] = sum over the agglomerate box nodes of chi_i psi_a . r
+template <typename T>
+__global__ void __launch_bounds__(PC_THREADS) k_restrict(
+    const T* __restrict__ r, long long stride, int nelx, int nely, int H, int ncx,
+    const int* __restrict__ type_of, const int* __restrict__ kept, const int* __restrict__ coff,
+    const T* __restrict__ psi, int kmax, double* __restrict__ rc, int Nt) {
+  __shared__ double sh[PC_THREADS / 32][MSTOPO_MAX_EIG];
+  const int i = blockIdx.x, s = blockIdx.y;
+  const int I = i % (ncx + 1), J = i / (ncx + 1);
+  const int t = type_of[i], k = kept[t];
+  const int N = 2 * H + 1;
+  const T* P = psi + (long long)t * N * N * 2 * kmax;
+  r += s * stride;
+  T acc[MSTOPO_MAX_EIG];
+  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) acc[a] = T(0);
+  // nodes with chi > 0: strictly inside the box
+  const int M = N - 2;
+  for (int u = threadIdx.x; u < M * M; u += blockDim.x) {
+    const int la = 1 + u % M, lb = 1 + u / M;
+    const int x = (I - 1) * H + la, y = (J - 1) * H + lb;
+    if (x < 0 || x > nelx || y < 0 || y > nely) continue;
+    const T chi = (T)(hat(x, I * H, H) * hat(y, J * H, H));
+    const long long node = (long long)y * (nelx + 1) + x;
+    const T rx = chi * r[2 * node], ry = chi * r[2 * node + 1];
+    const T* pp = P + ((long long)lb * N + la) * 2 * kmax;
+    for (int a = 0; a < k; ++a) acc[a] = fma(rx, pp[a], fma(ry, pp[kmax + a], acc[a]));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = 0; a < k; ++a) {
+    double v = (double)acc[a];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w][a] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double v = 0.0;
+    for (int q = 0; q < PC_THREADS / 32; ++q) v += sh[q][threadIdx.x];
+    rc[(long long)s * Nt + coff[i] + threadIdx.x] = v;
+  }
+}
+
+// uc[s] = Kcinv rc[s]   (one warp per row, all systems)
+__global__ void k_coarse_gemv(const double* __restrict__ Kinv, const double* __restrict__ rc,
+                              double* __restrict__ uc, int Nt, int nsys) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= Nt) return;
+  const double* row = Kinv + (long long)warp * Nt;
+  double acc[MSTOPO_MAX_SYS] = {0, 0, 0, 0};
+  for (int c = lane; c < Nt; c += 32) {
+    const double m = row[c];
+    for (int s = 0; s < nsys; ++s) acc[s] = fma(m, rc[(long long)s * Nt + c], acc[s]);
+  }
+  for (int s = 0; s < nsys; ++s) {
+    double v = acc[s];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) uc[(long long)s * Nt + warp] = v;
+  }
+}
+
+// Patch solves: one CTA per group of up to PC_GROUP agglomerates of one type, all systems.
+// Right-hand side columns: slot = g * nsys + s.  Work buffer Xg [group][NP][nbP][R].
+template <typename T>
+__global__ void __launch_bounds__(PC_THREADS) k_patch_solve(
+    const T* __restrict__ r, long long stride, int nsys, int nelx, int nely, int H, int ncx,
+    const int* __restrict__ grp_type, const int* __restrict__ grp_first,
+    const int* __restrict__ grp_count, const int* __restrict__ perm,
+    const T* __restrict__ Linv, const T* __restrict__ C, T* __restrict__ Xg) {
+  extern __shared__ unsigned char smraw[];
+  T* smem = reinterpret_cast<T*>(smraw);
+  const int g = blockIdx.x;
+  const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
+  const int N = 2 * H - 1, nb = 2 * N;
+  const int R = PC_GROUP * nsys;
+  const long long nn = (long long)nb * nb;
+  T* X = Xg + (long long)g * N * nb * R;
+  // gather: X[line][2a+c][p*nsys+s] = r_s(node) on the patch box (zero outside the mesh)
+  for (long long t = threadIdx.x; t < (long long)N * nb * R; t += blockDim.x) {
+    const int col = t % R;
+    const long long dof = t / R;
+    const int p = col / nsys, s = col % nsys;
+    T v = T(0);
+    if (p < cnt) {
+      const int ia = perm[first + p];
+      const int I = ia % (ncx + 1), J = ia / (ncx + 1);
+      const int line = dof / nb, rr = dof % nb;
+      const int x = (I - 1) * H + 1 + (rr >> 1), y = (J - 1) * H + 1 + line;
+      if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
+        v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (rr & 1)];
+    }
+    X[t] = v;
+  }
+  __syncthreads();
+  T* stage = smem;
+  T* t0 = stage + nn;
+  T* t1 = t0 + nb * R;
+  bt_solve<T, true>(Linv + (long long)type * N * nn, C + (long long)type * (N - 1) * nn, nb, N, X,
+                    R, stage, t0, t1);
+}
+
+// z(node) = sum over the (up to four) agglomerates around the node of
+//           chi_i psi_i uc_i  (coarse part)  +  patch solution of omega_i at the node
+template <typename T>
+__global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nelx, int nely,
+                          int H, int ncx, int ncy, const int* __restrict__ type_of,
+                          const int* __restrict__ kept, const int* __restrict__ coff,
+                          const T* __restrict__ psi, int kmax, const double* __restrict__ uc,
+                          int Nt, const int* __restrict__ agg_group,
+                          const int* __restrict__ agg_slot, const T* __restrict__ Xg,
+                          const uint8_t* __restrict__ nmask, int part) {
+  const long long nn1 = (long long)(nelx + 1) * (nely + 1);
+  const int s = blockIdx.y;
+  const int N = 2 * H + 1, NP = 2 * H - 1, nbP = 2 * NP;
+  const int R = PC_GROUP * nsys;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn1;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int x = node % (nelx + 1), y = node / (nelx + 1);
+    double zx = 0.0, zy = 0.0;
+    const int Ib = x / H, Jb = y / H;
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int I = Ib + di, J = Jb + dj;
+        if (I > ncx || J > ncy) continue;
+        if (abs(x - I * H) >= H || abs(y - J * H) >= H) continue;
+        const int i = J * (ncx + 1) + I;
+        if (part != 2) {
+          const int t = type_of[i], k = kept[t];
+          const double chi = hat(x, I * H, H) * hat(y, J * H, H);
+          const long long l = (long long)(y - (J - 1) * H) * N + (x - (I - 1) * H);
+          const T* pp = psi + ((long long)t * N * N + l) * 2 * kmax;
+          const double* u = uc + (long long)s * Nt + coff[i];
+          double ax = 0.0, ay = 0.0;
+          for (int a = 0; a < k; ++a) {
+            ax = fma((double)pp[a], u[a], ax);
+            ay = fma((double)pp[kmax + a], u[a], ay);
+          }
+          zx = fma(chi, ax, zx);
+          zy = fma(chi, ay, zy);
+        }
+        if (part != 1) {
+          const int la = x - (I - 1) * H - 1, lb = y - (J - 1) * H - 1;
+          const long long base = ((long long)agg_group[i] * NP + lb) * nbP + 2 * la;
+          const int col = agg_slot[i] * nsys + s;
+          zx += (double)Xg[base * R + col];
+          zy += (double)Xg[(base + 1) * R + col];
+        }
+      }
+    const uint8_t f = nmask[node];
+    z[s * stride + 2 * node] = (f & 1) ? T(0) : (T)zx;
+    z[s * stride + 2 * node + 1] = (f & 2) ? T(0) : (T)zy;
+  }
+}
+
+// ------------------------------------------------------------------------------ host side
+#define CKB(x)                                                                  \
+  do {                                                                          \
+    cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                    \
+      h->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x;      \
+      return e_ == cudaErrorMemoryAllocation ? MSTOPO_OUT_OF_MEMORY : MSTOPO_CUDA_ERROR; \
+    }                                                                           \
+  } while (0)
+
+static void dfree(void* p) { if (p) cudaFree(p); }
+
+void precond_free(Precond& pc) {
+  dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff); dfree(pc.d_perm);
+  dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count);
+  dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
+  dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
+  dfree(pc.d_Kc); dfree(pc.d_Kcinv); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
+  dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
+  pc = Precond();
+}
+
+// extra per-agglomerate maps for the combine kernel live behind d_rcpart (ints)
+static int* agg_group_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart); }
+static int* agg_slot_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart) + pc.Nc; }
+
+mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) {
+  Precond old = h->pc;
+  precond_free(old);
+  h->pc = Precond();
+  Precond& pc = h->pc;
+  cudaStream_t s = h->s;
+  const int H = h->p.H;
+  pc.H = H; pc.NA = 2 * H + 1; pc.NP = 2 * H - 1; pc.nbA = 2 * pc.NA; pc.nbP = 2 * pc.NP;
+  pc.ncx = h->nelx / H; pc.ncy = h->nely / H; pc.Nc = (pc.ncx + 1) * (pc.ncy + 1);
+  pc.kmax = h->p.n_eig;
+  pc.local_shift = h->p.precision == MSTOPO_MIXED ? h->p.local_shift : 0.0;
+  const double* E = h->d_E64 + (long long)ref * h->n_el;
+  K0P K0;
+  for (int q = 0; q < 64; ++q) K0.k[q] = h->K0[q];
+  cudaEvent_t ev[6];
+  for (int q = 0; q < 6; ++q) CKB(cudaEventCreate(&ev[q]));
+  CKB(cudaEventRecord(ev[0], s));
+  // 1. hashes -> types
+  unsigned long long* d_hash;
+  CKB(cudaMalloc(&d_hash, (size_t)pc.Nc * 16));
+  CKB(cudaMemsetAsync(d_hash, 0, (size_t)pc.Nc * 16, s));
+  k_hash_agg<<<pc.Nc, PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, H, pc.ncx, d_hash);
+  CKB(cudaGetLastError());
+  std::vector<unsigned long long> hh((size_t)pc.Nc * 2);
+  CKB(cudaMemcpyAsync(hh.data(), d_hash, (size_t)pc.Nc * 16, cudaMemcpyDeviceToHost, s));
+  CKB(cudaStreamSynchronize(s));
+  cudaFree(d_hash);
+  std::map<std::pair<unsigned long long, unsigned long long>, int> tmap;
+  pc.h_type_of_agg.resize(pc.Nc);
+  for (int i = 0; i < pc.Nc; ++i) {
+    auto key = std::make_pair(hh[2 * i], hh[2 * i + 1]);
+    auto it = tmap.find(key);
+    if (it == tmap.end()) {
+      int t = (int)pc.h_rep_agg.size();
+      tmap[key] = t;
+      pc.h_rep_agg.push_back(i);
+      pc.h_type_of_agg[i] = t;
+    } else {
+      pc.h_type_of_agg[i] = it->second;
+    }
+  }
+  const int T = pc.n_types = (int)pc.h_rep_agg.size();
+  int* d_rep;
+  CKB(cudaMalloc(&d_rep, T * sizeof(int)));
+  CKB(cudaMemcpyAsync(d_rep, pc.h_rep_agg.data(), T * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMalloc(&pc.d_type_of_agg, pc.Nc * sizeof(int)));
+  CKB(cudaMemcpyAsync(pc.d_type_of_agg, pc.h_type_of_agg.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaEventRecord(ev[1], s));
+
+  // 2. agglomerate matrices, shifted factor, eigen-solve
+  const int NA = pc.NA, nbA = pc.nbA;
+  const long long nnA = (long long)nbA * nbA, nA = (long long)NA * nbA;
+  const int q = std::min(2 * pc.kmax + 4, 2 * MSTOPO_MAX_EIG);
+  double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY;
+  uint8_t* dfree_;
+  int* d_st;
+  CKB(cudaMalloc(&dA, (size_t)T * NA * nnA * 8));
+  CKB(cudaMalloc(&dB, (size_t)T * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dLi, (size_t)T * NA * nnA * 8));
+  CKB(cudaMalloc(&dC, (size_t)T * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dS, (size_t)T * nnA * 8));
+  CKB(cudaMalloc(&dfree_, (size_t)T * nA));
+  CKB(cudaMalloc(&d_st, (size_t)std::max(T, 1) * sizeof(int)));
+  CKB(cudaMalloc(&dX, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dY, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dKY, (size_t)T * nA * q * 8));
+  k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
+                                                    pc.ncx, 0, 0, 0, K0, dA, dB, dfree_);
+  CKB(cudaGetLastError());
+  k_bt_factor<<<T, PC_THREADS, 0, s>>>(dA, dB, dfree_, EIG_SHIFT, nbA, NA, dLi, dC, dS, d_st);
+  CKB(cudaGetLastError());
+  CKB(cudaMalloc(&pc.d_lambda, (size_t)T * MSTOPO_MAX_EIG * 8));
+  CKB(cudaMemsetAsync(pc.d_lambda, 0, (size_t)T * MSTOPO_MAX_EIG * 8, s));
+  CKB(cudaMalloc(&pc.d_kept, T * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_eigres, T * 8));
+  CKB(cudaMalloc(&pc.d_eigsweeps, T * sizeof(int)));
+  EigArgs ea;
+  ea.E = E; ea.nmask = h->d_nmask; ea.nelx = h->nelx; ea.nely = h->nely; ea.H = H; ea.ncx = pc.ncx;
+  ea.rep = d_rep; ea.A = dA; ea.freem = dfree_; ea.Linv = dLi; ea.C = dC;
+  ea.X = dX; ea.Y = dY; ea.KY = dKY; ea.q = q; ea.kmax = pc.kmax; ea.lam_thresh = h->p.lambda_thresh;
+  ea.lambda = pc.d_lambda; ea.kept = pc.d_kept; ea.res = pc.d_eigres; ea.sweeps = pc.d_eigsweeps;
+  ea.K0 = K0;
+  size_t esm = (size_t)(nnA + 2 * nbA * q + 6 * q * q + 2 * q) * 8;
+  CKB(cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  k_eigen<<<T, PC_THREADS, esm, s>>>(ea);
+  CKB(cudaGetLastError());
+  std::vector<int> fst(T);
+  CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  pc.h_kept.resize(T);
+  CKB(cudaMemcpyAsync(pc.h_kept.data(), pc.d_kept, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKB(cudaStreamSynchronize(s));
+  for (int t = 0; t < T; ++t) {
+    if (fst[t] || pc.h_kept[t] < 1) {
+      h->err = "agglomerate eigenproblem failed (non-positive pivot or Rayleigh-Ritz breakdown)";
+      return MSTOPO_NOT_SPD;
+    }
+  }
+  CKB(cudaMalloc(&pc.d_psi64, (size_t)T * nA * pc.kmax * 8));
+  CKB(cudaMalloc(&pc.d_psi32, (size_t)T * nA * pc.kmax * 4));
+  k_store_psi<<<dim3(64, T), 256, 0, s>>>(dX, pc.d_kept, (int)nA, q, pc.kmax, pc.d_psi64, pc.d_psi32);
+  CKB(cudaGetLastError());
+  CKB(cudaEventRecord(ev[2], s));
+  cudaFree(dLi); cudaFree(dC); cudaFree(dS); cudaFree(dX); cudaFree(dY); cudaFree(dKY);
+  cudaFree(dA); cudaFree(dB); cudaFree(dfree_);
+
+  // 3. patch matrices and factors
+  const int NP = pc.NP, nbP = pc.nbP;
+  const long long nnP = (long long)nbP * nbP, nP = (long long)NP * nbP;
+  double *pA, *pB, *pS;
+  uint8_t* pfree;
+  CKB(cudaMalloc(&pA, (size_t)T * NP * nnP * 8));
+  CKB(cudaMalloc(&pB, (size_t)T * (NP - 1) * nnP * 8));
+  CKB(cudaMalloc(&pS, (size_t)T * nnP * 8));
+  CKB(cudaMalloc(&pfree, (size_t)T * nP));
+  CKB(cudaMalloc(&pc.d_pLinv64, (size_t)T * NP * nnP * 8));
+  CKB(cudaMalloc(&pc.d_pC64, (size_t)T * (NP - 1) * nnP * 8));
+  // elements touching the inner nodes: the whole agglomerate (offset window 0)
+  k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
+                                                    pc.ncx, 1, 0, 0, K0, pA, pB, pfree);
+  CKB(cudaGetLastError());
+  k_bt_factor<<<T, PC_THREADS, 0, s>>>(pA, pB, pfree, pc.local_shift, nbP, NP, pc.d_pLinv64,
+                                       pc.d_pC64, pS, d_st);
+  CKB(cudaGetLastError());
+  CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKB(cudaMalloc(&pc.d_pLinv32, (size_t)T * NP * nnP * 4));
+  CKB(cudaMalloc(&pc.d_pC32, (size_t)T * (NP - 1) * nnP * 4));
+  k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pLinv64, pc.d_pLinv32, (long long)T * NP * nnP);
+  k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pC64, pc.d_pC32, (long long)T * (NP - 1) * nnP);
+  CKB(cudaGetLastError());
+  CKB(cudaStreamSynchronize(s));
+  cudaFree(pA); cudaFree(pB); cudaFree(pS); cudaFree(pfree); cudaFree(d_rep);
+  for (int t = 0; t < T; ++t)
+    if (fst[t]) {
+      h->err = "patch matrix not positive definite";
+      return MSTOPO_NOT_SPD;
+    }
+  CKB(cudaEventRecord(ev[3], s));
+
+  // 4. coarse space: offsets, line mapping, assembly, factor, dense inverse
+  pc.h_coff.resize(pc.Nc + 1);
+  pc.h_coff[0] = 0;
+  for (int i = 0; i < pc.Nc; ++i) pc.h_coff[i + 1] = pc.h_coff[i] + pc.h_kept[pc.h_type_of_agg[i]];
+  const int Nt = pc.Nt = pc.h_coff[pc.Nc];
+  CKB(cudaMalloc(&pc.d_coff, (pc.Nc + 1) * sizeof(int)));
+  CKB(cudaMemcpyAsync(pc.d_coff, pc.h_coff.data(), (pc.Nc + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CoarseMap cm;
+  cm.by_columns = (pc.ncy + 1) <= (pc.ncx + 1);
+  cm.ncx = pc.ncx; cm.ncy = pc.ncy; cm.kmax = pc.kmax;
+  const int NLc = cm.by_columns ? pc.ncx + 1 : pc.ncy + 1;
+  const int per_line = cm.by_columns ? pc.ncy + 1 : pc.ncx + 1;
+  const int nbc = per_line * pc.kmax;
+  const long long nnc = (long long)nbc * nbc;
+  std::vector<int> slot2orig((size_t)NLc * nbc, -1);
+  for (int J = 0; J <= pc.ncy; ++J)
+    for (int I = 0; I <= pc.ncx; ++I) {
+      int i = J * (pc.ncx + 1) + I;
+      int L = cm.by_columns ? I : J, P = cm.by_columns ? J : I;
+      int k = pc.h_kept[pc.h_type_of_agg[i]];
+      for (int a = 0; a < k; ++a) slot2orig[(size_t)L * nbc + P * pc.kmax + a] = pc.h_coff[i] + a;
+    }
+  int* d_s2o;
+  double *cA, *cB, *cLi, *cC, *cS, *cX;
+  CKB(cudaMalloc(&d_s2o, slot2orig.size() * sizeof(int)));
+  CKB(cudaMemcpyAsync(d_s2o, slot2orig.data(), slot2orig.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMalloc(&cA, (size_t)NLc * nnc * 8));
+  CKB(cudaMalloc(&cB, (size_t)std::max(NLc - 1, 1) * nnc * 8));
+  CKB(cudaMalloc(&cLi, (size_t)NLc * nnc * 8));
+  CKB(cudaMalloc(&cC, (size_t)std::max(NLc - 1, 1) * nnc * 8));
+  CKB(cudaMalloc(&cS, (size_t)nnc * 8));
+  CKB(cudaMemsetAsync(cA, 0, (size_t)NLc * nnc * 8, s));
+  CKB(cudaMemsetAsync(cB, 0, (size_t)std::max(NLc - 1, 1) * nnc * 8, s));
+  k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(E, h->nelx, h->nely, H, pc.d_type_of_agg,
+                                                          pc.d_kept, pc.d_psi64, pc.kmax, K0, cm,
+                                                          cA, cB, nbc);
+  CKB(cudaGetLastError());
+  // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
+  k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, nbc, NLc, cLi, cC, cS, d_st);
+  CKB(cudaGetLastError());
+  int cst = 0;
+  CKB(cudaMemcpyAsync(&cst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKB(cudaMalloc(&pc.d_Kcinv, (size_t)Nt * Nt * 8));
+  const int nblk = cdiv((long long)NLc * nbc, RC);
+  CKB(cudaMalloc(&cX, (size_t)nblk * NLc * nbc * RC * 8));
+  CKB(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nbc * RC * 8));
+  k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi, cC, nbc, NLc, d_s2o, Nt, cX, pc.d_Kcinv);
+  CKB(cudaGetLastError());
+  CKB(cudaStreamSynchronize(s));
+  cudaFree(cA); cudaFree(cB); cudaFree(cLi); cudaFree(cC); cudaFree(cS); cudaFree(cX); cudaFree(d_s2o);
+  if (cst) {
+    h->err = "coarse matrix K_c not positive definite";
+    return MSTOPO_NOT_SPD;
+  }
+  CKB(cudaEventRecord(ev[4], s));
+
+  // 5. patch-solve work groups (per type, PC_GROUP agglomerates each) and apply buffers
+  std::vector<std::vector<int>> by_type(T);
+  for (int i = 0; i < pc.Nc; ++i) by_type[pc.h_type_of_agg[i]].push_back(i);
+  std::vector<int> perm, gt, gf, gc, agg_group(pc.Nc), agg_slot(pc.Nc);
+  for (int t = 0; t < T; ++t)
+    for (size_t b = 0; b < by_type[t].size(); b += PC_GROUP) {
+      int g = (int)gt.size();
+      gt.push_back(t);
+      gf.push_back((int)perm.size());
+      int c = (int)std::min<size_t>(PC_GROUP, by_type[t].size() - b);
+      gc.push_back(c);
+      for (int p = 0; p < c; ++p) {
+        int i = by_type[t][b + p];
+        agg_group[i] = g;
+        agg_slot[i] = p;
+        perm.push_back(i);
+      }
+    }
+  pc.n_groups = (int)gt.size();
+  CKB(cudaMalloc(&pc.d_perm, perm.size() * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_grp_type, gt.size() * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_grp_first, gf.size() * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_grp_count, gc.size() * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_rcpart, (size_t)2 * pc.Nc * sizeof(int)));
+  CKB(cudaMemcpyAsync(pc.d_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(pc.d_grp_type, gt.data(), gt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(pc.d_grp_first, gf.data(), gf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(pc.d_grp_count, gc.data(), gc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(agg_group_ptr(pc), agg_group.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(agg_slot_ptr(pc), agg_slot.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
+  CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
+  const size_t xg = (size_t)pc.n_groups * nP * PC_GROUP * MSTOPO_MAX_SYS;
+  CKB(cudaMalloc(&pc.d_zp32, xg * 4));
+  CKB(cudaMalloc(&pc.d_zp64, xg * 8));
+  CKB(cudaEventRecord(ev[5], s));
+  // build report
+  std::vector<double> eres(T);
+  std::vector<int> esw(T);
+  CKB(cudaMemcpyAsync(eres.data(), pc.d_eigres, T * 8, cudaMemcpyDeviceToHost, s));
+  CKB(cudaMemcpyAsync(esw.data(), pc.d_eigsweeps, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKB(cudaStreamSynchronize(s));
+  if (info) {
+    info->n_agglomerates = pc.Nc;
+    info->n_types = T;
+    info->n_coarse = Nt;
+    info->eig_sweeps = *std::max_element(esw.begin(), esw.end());
+    info->eig_residual = *std::max_element(eres.begin(), eres.end());
+    cudaEventElapsedTime(&info->ms_hash, ev[0], ev[1]);
+    cudaEventElapsedTime(&info->ms_eigen, ev[1], ev[2]);
+    cudaEventElapsedTime(&info->ms_patch_factor, ev[2], ev[3]);
+    cudaEventElapsedTime(&info->ms_coarse, ev[3], ev[4]);
+    cudaEventElapsedTime(&info->ms_total, ev[0], ev[5]);
+  }
+  for (int q2 = 0; q2 < 6; ++q2) cudaEventDestroy(ev[q2]);
+  pc.built = 1;
+  return MSTOPO_OK;
+}
+
+template <typename T>
+static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int part,
+                              const T* psi, const T* Linv, const T* C, T* Xg) {
+  Precond& pc = h->pc;
+  cudaStream_t s = h->s;
+  const long long n = h->n_dof;
+  if (part != 2) {
+    k_restrict<T><<<dim3(pc.Nc, nsys), PC_THREADS, 0, s>>>(r, n, h->nelx, h->nely, pc.H, pc.ncx,
+                                                          pc.d_type_of_agg, pc.d_kept, pc.d_coff,
+                                                          psi, pc.kmax, pc.d_rc, pc.Nt);
+    k_coarse_gemv<<<cdiv((long long)pc.Nt * 32, 256), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, nsys);
+  }
+  if (part != 1) {
+    const int NP = pc.NP, nbP = pc.nbP, R = PC_GROUP * nsys;
+    size_t sm = ((size_t)nbP * nbP + 2 * (size_t)nbP * R) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_patch_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_patch_solve<T><<<pc.n_groups, PC_THREADS, sm, s>>>(r, n, nsys, h->nelx, h->nely, pc.H, pc.ncx,
+                                                          pc.d_grp_type, pc.d_grp_first,
+                                                          pc.d_grp_count, pc.d_perm, Linv, C, Xg);
+    (void)NP;
+  }
+  k_combine<T><<<dim3(608, nsys), 256, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
+                                               pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
+                                               pc.d_uc, pc.Nt, agg_group_ptr(pc), agg_slot_ptr(pc), Xg,
+                                               h->d_nmask, part);
+  return cudaGetLastError();
+}
+
+cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int nsys, int part) {
+  Precond& pc = h->pc;
+  return apply_impl<double>(h, r, z, nsys, part, pc.d_psi64, pc.d_pLinv64, pc.d_pC64, pc.d_zp64);
+}
+
+cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int nsys, int part) {
+  Precond& pc = h->pc;
+  return apply_impl<float>(h, r, z, nsys, part, pc.d_psi32, pc.d_pLinv32, pc.d_pC32, pc.d_zp32);
+}

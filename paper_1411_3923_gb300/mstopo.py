@@ -1,0 +1,255 @@
+"""Thin Python binding of the mstopo C ABI (include/mstopo.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``_lib/libmstopo.so``.  PyTorch supplies device memory; arrays are passed as raw pointers.
+There is no CPU fallback: if the shared library is missing the first use raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmstopo.so")
+
+FP64, MIXED = 0, 1
+FIELD_RHO_TILDE, FIELD_RHO_BAR, FIELD_YOUNG = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA_ERROR", 4: "NOT_SPD",
+          5: "MAX_ITER", 6: "NONFINITE", 7: "TIMEOUT", 8: "NOT_READY"}
+
+
+class MstopoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Problem(C.Structure):
+    _fields_ = [("nelx", C.c_int32), ("nely", C.c_int32), ("nu", C.c_double), ("E0", C.c_double),
+                ("Emin", C.c_double), ("penal", C.c_double), ("fixed", C.c_void_p),
+                ("H", C.c_int32), ("n_eig", C.c_int32), ("lambda_thresh", C.c_double),
+                ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("local_shift", C.c_double), ("stream", C.c_void_p)]
+
+
+class _BuildInfo(C.Structure):
+    _fields_ = [("n_agglomerates", C.c_int32), ("n_types", C.c_int32), ("n_coarse", C.c_int32),
+                ("eig_sweeps", C.c_int32), ("eig_residual", C.c_double), ("ms_hash", C.c_float),
+                ("ms_eigen", C.c_float), ("ms_patch_factor", C.c_float), ("ms_coarse", C.c_float),
+                ("ms_total", C.c_float)]
+
+
+class _SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("replacements", C.c_int32),
+                ("rel_residual", C.c_double), ("compliance", C.c_double), ("ms", C.c_float)]
+
+
+_lib = None
+
+SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_dofs",
+           "mstopo_num_realisations", "mstopo_set_design", "mstopo_get_field",
+           "mstopo_build_preconditioner", "mstopo_solve", "mstopo_solve_host",
+           "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
+           "mstopo_apply_precond", "mstopo_get_eigenpairs"]
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (no GPU work happens here)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"mstopo CUDA library not built ({path} missing); run "
+                           "paper_1411_3923_gb300._build.build() first")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "mstopo_create": ([C.POINTER(_Problem), C.POINTER(vp)], i32),
+        "mstopo_destroy": ([vp], None),
+        "mstopo_last_error": ([vp], C.c_char_p),
+        "mstopo_num_dofs": ([vp], i64),
+        "mstopo_num_realisations": ([vp], i32),
+        "mstopo_set_design": ([vp, vp, i64, dbl, dbl, vp, i32, i32, i32], i32),
+        "mstopo_get_field": ([vp, i32, i32, vp], i32),
+        "mstopo_build_preconditioner": ([vp, i32, C.POINTER(_BuildInfo)], i32),
+        "mstopo_solve": ([vp, i32, vp, vp, vp, vp], i32),
+        "mstopo_solve_host": ([vp, i32, vp, vp, vp, vp], i32),
+        "mstopo_compliance_and_sensitivity": ([vp, dbl, vp, vp, vp], i32),
+        "mstopo_apply_K": ([vp, i32, i32, vp, vp], i32),
+        "mstopo_apply_K_f32": ([vp, i32, vp, vp], i32),
+        "mstopo_apply_precond": ([vp, i32, i32, vp, vp], i32),
+        "mstopo_get_eigenpairs": ([vp, i32, i32, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _dev(t: torch.Tensor, dtype=torch.float64) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    return t.detach().to(dtype).contiguous()
+
+
+class Problem:
+    """One mesh with its boundary conditions: design chain, preconditioner and solves."""
+
+    def __init__(self, nelx: int, nely: int, fixed: np.ndarray, *, nu: float = 0.3,
+                 E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
+                 n_eig: int = 4, lambda_thresh: float = 0.0, precision: str = "mixed",
+                 tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
+                 stream: Optional[int] = None):
+        lib = load()
+        self.nelx, self.nely = nelx, nely
+        self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
+        assert self._fixed.size == 2 * (nelx + 1) * (nely + 1)
+        d = _Problem(nelx, nely, nu, E0, Emin, penal, self._fixed.ctypes.data, H, n_eig,
+                     lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
+                     local_shift, stream)
+        h = C.c_void_p()
+        st = lib.mstopo_create(C.byref(d), C.byref(h))
+        if st != 0:
+            raise MstopoError(st, lib.mstopo_last_error(None).decode())
+        self._h = h
+        self.n_dof = int(lib.mstopo_num_dofs(h))
+        self.n_eta = 0
+        self.n_design = 0
+        self.precision = precision
+
+    def _check(self, st: int):
+        if st != 0:
+            raise MstopoError(st, _lib.mstopo_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mstopo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- design chain ---------------------------------------------------------------
+    def set_design(self, rho: torch.Tensor, rmin: float, beta: float, etas: Sequence[float],
+                   cell: Optional[tuple] = None):
+        rho = _dev(rho)
+        eta = np.ascontiguousarray(etas, dtype=np.float64)
+        cx, cy = (cell if cell else (0, 0))
+        self._check(_lib.mstopo_set_design(self._h, _ptr(rho), rho.numel(), rmin, beta,
+                                           eta.ctypes.data, eta.size, cx, cy))
+        self.n_eta, self.n_design = int(eta.size), rho.numel()
+        self.design_shape = (cy, cx) if cell else (self.nely, self.nelx)
+
+    def get_field(self, field: int, realisation: int = 0) -> torch.Tensor:
+        shape = (self.nely, self.nelx) if field == FIELD_YOUNG else self.design_shape
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        self._check(_lib.mstopo_get_field(self._h, field, realisation, _ptr(out)))
+        return out
+
+    # ---- preconditioner -------------------------------------------------------------
+    def build_preconditioner(self, ref: int = -1) -> dict:
+        info = _BuildInfo()
+        self._check(_lib.mstopo_build_preconditioner(self._h, ref, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in _BuildInfo._fields_}
+
+    # ---- solves -----------------------------------------------------------------------
+    def _nsys(self, realisation: int) -> int:
+        return self.n_eta if realisation < 0 else 1
+
+    def solve(self, f: torch.Tensor, realisation: int = -1, u0: Optional[torch.Tensor] = None):
+        f = _dev(f)
+        ns = self._nsys(realisation)
+        u = torch.empty((ns, self.nely + 1, self.nelx + 1, 2), dtype=torch.float64, device="cuda")
+        infos = (_SolveInfo * ns)()
+        u0p = _ptr(_dev(u0)) if u0 is not None else None
+        st = _lib.mstopo_solve(self._h, realisation, _ptr(f), _ptr(u), u0p, infos)
+        out = [{k: getattr(i, k) for k, _ in _SolveInfo._fields_} for i in infos]
+        self._check(st)
+        return u, out
+
+    def solve_host(self, f: np.ndarray, realisation: int = -1, u: Optional[np.ndarray] = None,
+                   u0: Optional[np.ndarray] = None):
+        """Solve with host arrays (copies in and out are part of the call)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        ns = self._nsys(realisation)
+        if u is None:
+            u = np.empty((ns, self.nely + 1, self.nelx + 1, 2), dtype=np.float64)
+        infos = (_SolveInfo * ns)()
+        st = _lib.mstopo_solve_host(self._h, realisation, f.ctypes.data, u.ctypes.data,
+                                    None if u0 is None else np.ascontiguousarray(u0).ctypes.data, infos)
+        out = [{k: getattr(i, k) for k, _ in _SolveInfo._fields_} for i in infos]
+        self._check(st)
+        return u, out
+
+    def compliance_and_sensitivity(self, kappa: float = 1.0, want_grad: bool = True):
+        c = np.zeros(self.n_eta)
+        fr = C.c_double()
+        g = torch.empty(self.design_shape, dtype=torch.float64, device="cuda") if want_grad else None
+        self._check(_lib.mstopo_compliance_and_sensitivity(self._h, kappa, c.ctypes.data,
+                                                           C.addressof(fr), _ptr(g)))
+        return c, fr.value, g
+
+    # ---- kernel-level entry points ----------------------------------------------------
+    def apply_K(self, u: torch.Tensor, realisation: int = 0, precision: int = FP64) -> torch.Tensor:
+        u = _dev(u)
+        y = torch.empty_like(u)
+        self._check(_lib.mstopo_apply_K(self._h, realisation, precision, _ptr(u), _ptr(y)))
+        return y
+
+    def apply_K_f32(self, u: torch.Tensor, realisation: int = 0, out: Optional[torch.Tensor] = None):
+        u = _dev(u, torch.float32)
+        y = torch.empty_like(u) if out is None else out
+        self._check(_lib.mstopo_apply_K_f32(self._h, realisation, _ptr(u), _ptr(y)))
+        return y
+
+    def apply_precond(self, r: torch.Tensor, precision: int = FP64, part: int = 0) -> torch.Tensor:
+        r = _dev(r)
+        z = torch.empty_like(r)
+        self._check(_lib.mstopo_apply_precond(self._h, precision, part, _ptr(r), _ptr(z)))
+        return z
+
+    def get_eigenpairs(self, I: int, J: int, n_eig: int, H: int):
+        lam = np.zeros(n_eig)
+        psi = np.zeros((2 * H + 1, 2 * H + 1, 2, n_eig))
+        k = C.c_int32()
+        self._check(_lib.mstopo_get_eigenpairs(self._h, I, J, lam.ctypes.data, psi.ctypes.data,
+                                               C.addressof(k)))
+        return lam[:k.value], psi[..., :k.value], k.value
+
+
+class RobustCompliance(torch.autograd.Function):
+    """f(rho) = mean_k f^T u_k + kappa std_k f^T u_k (Sec. 4.4) with the hand-written adjoint
+    (self-adjoint sensitivity chained through SIMP, projection, tiling and the filter)."""
+
+    @staticmethod
+    def forward(ctx, rho, prob: Problem, f, rmin, beta, etas, cell, kappa):
+        prob.set_design(rho, rmin, beta, etas, cell)
+        prob.build_preconditioner(-1)
+        prob.solve(f, -1)
+        c, fr, g = prob.compliance_and_sensitivity(kappa, want_grad=True)
+        ctx.save_for_backward(g)
+        return torch.tensor(fr, dtype=torch.float64, device=rho.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out * g, None, None, None, None, None, None, None

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle, element by element.
+
+Tolerances (derived from the arithmetic):
+  design chain (FP64)      1e-12 relative: a few roundings of tanh/pow/filter sums
+  FP64 matvec              1e-12 of sum_e |E_e K0| |u_e| per DOF (summation order only)
+  FP32 matvec              2e-6 of the same scale (FP32 unit round-off x ~30 terms)
+  patch solves (FP64)      1e-9 relative (block Cholesky vs sparse LU of the same matrix)
+  solve u (FP64 and MIXED) energy-norm error <= 1e-6 at true residual 1e-10, compliance 1e-9
+  design gradient          2-norm relative 1e-7 against the oracle's chain on the same u
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads
+from oracle import design, fem, msfem, pipeline
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1411_3923_gb300 as m
+    return m
+
+
+def make_problem(m, wl, precision="fp64", **kw):
+    return m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin, penal=wl.penal,
+                     H=wl.H, n_eig=wl.n_eig, precision=precision, tol=kw.pop("tol", 1e-10), **kw)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("cell", [None, (8, 4)])
+@pytest.mark.parametrize("size", [(24, 12), (40, 16)])
+def test_design_chain(cell, size):
+    m = _gpu()
+    wl = workloads.small(*size, seed=11, kind="random", cell=cell, etas=(0.3, 0.5, 0.7),
+                         rmin=2.3, beta=8.0, H=4)
+    prob = make_problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    _, _, _, chain = pipeline.build(wl)
+    ref = chain.forward(wl.rho)
+    rt = prob.get_field(m.FIELD_RHO_TILDE).cpu().numpy()
+    assert np.allclose(rt, ref["rho_tilde"], rtol=1e-12, atol=1e-14)
+    for k in range(3):
+        rb = prob.get_field(m.FIELD_RHO_BAR, k).cpu().numpy()
+        assert np.allclose(rb, ref["rho_bar"][k], rtol=1e-12, atol=1e-14)
+        E = prob.get_field(m.FIELD_YOUNG, k).cpu().numpy()
+        assert np.allclose(E, ref["E"][k], rtol=1e-12, atol=1e-20)
+
+
+@pytest.mark.parametrize("size", [(7 * 4, 3 * 4), (33 * 4, 5 * 4), (64, 64)])
+def test_matvec_fp64_and_fp32(size):
+    m = _gpu()
+    wl = workloads.small(*size, seed=3, kind="random", H=4)
+    prob = make_problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    E = prob.get_field(m.FIELD_YOUNG, 0).cpu().numpy()
+    grid, K0, oprob, _ = pipeline.build(wl)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((wl.nely + 1, wl.nelx + 1, 2))
+    y_ref = oprob.apply(E, u)
+    # scale: sum_e |E_e K0| |u_e| per DOF
+    ue = np.abs(grid.nodal_from_neutral(u)); ue[oprob.fixed] = 0
+    scale = grid.nodal_to_neutral(fem.matvec_unconstrained(grid, grid.element_from_neutral(E), np.abs(K0), ue))
+    y64 = prob.apply_K(cuda(u), 0, m.FP64).cpu().numpy()
+    assert np.all(np.abs(y64 - y_ref) <= 1e-12 * scale + 1e-300)
+    y32 = prob.apply_K(cuda(u), 0, m.MIXED).cpu().numpy()
+    assert np.all(np.abs(y32 - y_ref) <= 2e-6 * scale + 1e-30)
+
+
+def test_patch_solves_match_sparse_lu():
+    m = _gpu()
+    wl = workloads.small(32, 16, seed=4, kind="voids", H=8, n_eig=4)
+    prob = make_problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    grid, K0, oprob, chain = pipeline.build(wl)
+    E = chain.forward(wl.rho)["E"][0]
+    tl = msfem.TwoLevel(oprob, E, wl.H, wl.n_eig)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal((wl.nely + 1, wl.nelx + 1, 2))
+    rf = grid.nodal_from_neutral(r)[oprob.free]
+    z_ref = np.zeros(grid.n_dof)
+    z_ref[oprob.free] = tl.local(rf)
+    z_ref = grid.nodal_to_neutral(z_ref)
+    z = prob.apply_precond(cuda(r), m.FP64, 2).cpu().numpy()
+    assert np.linalg.norm(z - z_ref) <= 1e-9 * np.linalg.norm(z_ref)
+    z32 = prob.apply_precond(cuda(r), m.MIXED, 2).cpu().numpy()
+    # FP32 factors of a contrast-1e9 matrix: compare in the energy of the patch matrices
+    assert np.linalg.norm(z32 - z_ref) <= 1e-2 * np.linalg.norm(z_ref)
+
+
+def test_eigenpairs_satisfy_generalised_eigenproblem():
+    """Every kept pair satisfies K_w psi = lambda diag(K_w) psi (Sec. 2.4, 3.2) with the
+    oracle's assembled agglomerate matrix, and the eigenvalues match the oracle's."""
+    m = _gpu()
+    wl = workloads.small(32, 16, seed=8, kind="random", H=8, n_eig=4)
+    prob = make_problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    grid, K0, oprob, chain = pipeline.build(wl)
+    E = chain.forward(wl.rho)["E"][0]
+    for (I, J) in [(0, 0), (2, 1), (4, 2), (1, 2)]:
+        lam, psi, k = prob.get_eigenpairs(I, J, wl.n_eig, wl.H)
+        a = msfem.Agglomerate(I, J, wl.H, wl.nelx, wl.nely)
+        keep = ~oprob.fixed[a.global_dofs(grid)]
+        Kw = a.local_stiffness(E, K0)[keep][:, keep]
+        D = Kw.diagonal()
+        # gather the GPU vectors on the (clipped) agglomerate nodes, oracle local order
+        bx, by = (I - 1) * wl.H, (J - 1) * wl.H
+        P = psi[a.node_j - by, a.node_i - bx]            # [nodes, 2, k]
+        P = P.reshape(-1, k)[keep]
+        R = Kw @ P - (D[:, None] * P) * lam[None, :]
+        assert np.sqrt(np.sum(R * R / D[:, None], axis=0)).max() < 1e-6
+        assert np.allclose(P.T @ (D[:, None] * P), np.eye(k), atol=1e-8)
+        lam_ref, _ = msfem.local_eigenpairs(Kw, k)
+        assert np.allclose(lam, lam_ref, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["voids", "random_periodic"])
+def test_solve_compliance_and_gradient(precision, case):
+    m = _gpu()
+    if case == "voids":
+        wl = workloads.small(48, 16, seed=6, kind="voids", H=8, n_eig=4, etas=(0.3, 0.5, 0.7),
+                             rmin=2.0, beta=8.0)
+    else:
+        wl = workloads.small(48, 24, seed=7, kind="random", H=8, n_eig=6, cell=(8, 8),
+                             etas=(0.5,), rmin=1.5, beta=4.0)
+    prob = make_problem(m, wl, precision, tol=1e-10)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    u, infos = prob.solve(cuda(wl.force), -1)
+    ref = pipeline.run(wl, "direct")
+    grid, K0, oprob, _ = pipeline.build(wl)
+    for k, info in enumerate(infos):
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+        Kf = oprob.free_matrix(ref["E"][k])
+        ug = grid.nodal_from_neutral(u[k].cpu().numpy())[oprob.free]
+        ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
+        assert msfem.energy_error(Kf, ur, ug) < 1e-6
+        assert info["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
+    c, fr, g = prob.compliance_and_sensitivity(1.0)
+    assert np.allclose(c, ref["c"], rtol=1e-9)
+    assert fr == pytest.approx(ref["f_robust"], rel=1e-9)
+    g = g.cpu().numpy()
+    assert np.linalg.norm(g - ref["dfdrho"]) <= 1e-7 * np.linalg.norm(ref["dfdrho"]) + 1e-12
+
+
+def test_host_pointer_solve_matches_device_solve():
+    m = _gpu()
+    wl = workloads.small(32, 16, seed=9, kind="voids", H=8, n_eig=4)
+    prob = make_problem(m, wl, "mixed", tol=1e-8)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    u_d, _ = prob.solve(cuda(wl.force), 0)
+    u_h, _ = prob.solve_host(wl.force, 0)
+    assert np.array_equal(u_d.cpu().numpy(), u_h)   # same kernels, deterministic reductions
+
+
+def test_mbb_c1_full_size_against_direct_solve():
+    """The 192x64 MBB workload (25,090 DOFs), mixed precision, against sparse LU."""
+    m = _gpu()
+    wl = workloads.make("mbb_c1")
+    prob = make_problem(m, wl, "mixed", tol=1e-8)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    info = prob.build_preconditioner()
+    assert info["n_agglomerates"] == 65 and info["n_coarse"] == 260
+    u, infos = prob.solve(cuda(wl.force), -1)
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    assert infos[0]["status"] == 0 and infos[0]["rel_residual"] <= 1e-8
+    assert infos[0]["compliance"] == pytest.approx(ref["c"][0], rel=1e-6)

@@ -1,0 +1,46 @@
+"""CPU-side checks of the C-ABI library: it loads and exports every symbol include/mstopo.h
+declares (no compute calls: those need a GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mstopo.h")).read()
+    return sorted(set(re.findall(r"\b(mstopo_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_symbols():
+    from paper_1411_3923_gb300 import SYMBOLS
+    assert sorted(SYMBOLS) == declared_symbols()
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    from paper_1411_3923_gb300 import _build
+    try:
+        _build.nvcc()
+    except RuntimeError:
+        pytest.skip("no CUDA toolkit")
+    path = _build.build()
+    import ctypes
+    lib = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_invalid_problem_is_rejected_without_gpu_work():
+    """mstopo_create validates its arguments before touching the device."""
+    import ctypes
+    import numpy as np
+    import paper_1411_3923_gb300 as m
+    from paper_1411_3923_gb300 import mstopo
+    lib = m.load()
+    fixed = np.zeros(2 * 9 * 5, np.uint8)
+    d = mstopo._Problem(8, 4, 0.3, 1.0, 1e-9, 3.0, fixed.ctypes.data, 3, 4, 0.0, 1, 1e-8, 100, 0.0, None)
+    h = ctypes.c_void_p()
+    assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1      # 8 % 3 != 0
+    assert h.value is None
+    assert b"invalid" in lib.mstopo_last_error(None)
