@@ -169,6 +169,20 @@ mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t 
 mstopo_status mstopo_get_eigenpairs(mstopo_handle* h, int32_t I, int32_t J, double* lambda,
                                     double* psi, int32_t* n_kept);
 
+/* ---- measurement (not part of the paper's method) ----------------------------------- */
+
+typedef struct {
+  int64_t launches;            /* kernels launched by this library in this process so far    */
+  int64_t kernel_launches[4];  /* profiled launches: [0] patch solves, [1] FP32 matvec,         */
+  double kernel_ms[4];         /* [2] FP64 matvec, [3] coarse solve; device ms summed (events) */
+} mstopo_stats;
+
+/* Turn per-kernel event timing on (1) or off (0) for this handle; resets its counters.
+ * While on, every profiled launch is bracketed by two CUDA events on the handle's stream. */
+mstopo_status mstopo_set_profiling(mstopo_handle* h, int32_t on);
+/* Counters: out is HOST.  Synchronises the handle's stream. */
+mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

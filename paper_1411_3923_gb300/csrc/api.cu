@@ -25,6 +25,45 @@
   } while (0)
 
 static thread_local std::string g_create_error;
+std::atomic<long long> g_launch_count{0};
+
+cudaEvent_t prof_begin(Prof& p, cudaStream_t s) {
+  cudaEvent_t e = nullptr;
+  if (!p.on) return e;
+  if (!p.pool.empty()) { e = p.pool.back(); p.pool.pop_back(); }
+  else if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, s);
+  return e;
+}
+
+void prof_end(Prof& p, int which, cudaEvent_t a, cudaStream_t s) {
+  if (!p.on || !a) return;
+  cudaEvent_t b = nullptr;
+  if (!p.pool.empty()) { b = p.pool.back(); p.pool.pop_back(); }
+  else if (cudaEventCreate(&b) != cudaSuccess) return;
+  cudaEventRecord(b, s);
+  p.pend.push_back({which, a, b});
+}
+
+void prof_collect(Prof& p) {
+  for (auto& q : p.pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      p.ms[q.which] += ms;
+      p.n[q.which] += 1;
+    }
+    p.pool.push_back(q.a);
+    p.pool.push_back(q.b);
+  }
+  p.pend.clear();
+}
+
+void prof_free(Prof& p) {
+  for (auto& q : p.pend) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+  for (auto e : p.pool) cudaEventDestroy(e);
+  p.pend.clear();
+  p.pool.clear();
+}
 
 extern "C" {
 
@@ -91,6 +130,7 @@ void mstopo_destroy(mstopo_handle* h) {
   else cudaDeviceSynchronize();
   precond_free(h->pc);
   solver_free(h->sv);
+  prof_free(h->prof);
   void* ptrs[] = {h->d_K0, h->d_nmask, h->d_rho, h->d_rho_tilde, h->d_wsum, h->d_rbar, h->d_drbar,
                   h->d_E64, h->d_E32, h->d_gfine, h->d_gdesign, h->d_w, h->d_flag, h->d_u_all,
                   h->d_f_all, h->d_host_stage};
@@ -317,6 +357,7 @@ mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t 
   CHECK_ARG(r && z, "null pointer");
   CHECK_ARG(part >= 0 && part <= 2, "part must be 0, 1 or 2");
   const long long n = h->n_dof;
+  CKA(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), h->s));
   double* rm;
   CKA(cudaMallocAsync(&rm, n * 8, h->s));
   CKA(launch_mask_copy(r, rm, h->d_nmask, h->n_nodes, 1, n, h->s));
@@ -333,7 +374,10 @@ mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t 
     CKA(cudaFreeAsync(b, h->s));
   }
   CKA(cudaFreeAsync(rm, h->s));
+  int werr = 0;
+  CKA(cudaMemcpyAsync(&werr, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CKA(cudaStreamSynchronize(h->s));
+  if (werr) { h->err = "bounded device wait gave up"; return MSTOPO_TIMEOUT; }
   return MSTOPO_OK;
 }
 
@@ -352,6 +396,27 @@ mstopo_status mstopo_get_eigenpairs(mstopo_handle* h, int32_t I, int32_t J, doub
   if (psi) CKA(cudaMemcpyAsync(psi, pc.d_psi64 + (size_t)t * nA * pc.kmax, nA * pc.kmax * 8,
                                cudaMemcpyDeviceToHost, h->s));
   CKA(cudaStreamSynchronize(h->s));
+  return MSTOPO_OK;
+}
+
+mstopo_status mstopo_set_profiling(mstopo_handle* h, int32_t on) {
+  if (!h) return MSTOPO_INVALID_ARG;
+  CKA(cudaStreamSynchronize(h->s));
+  prof_collect(h->prof);
+  h->prof.on = on ? 1 : 0;
+  for (int k = 0; k < PROF_N; ++k) { h->prof.ms[k] = 0.0; h->prof.n[k] = 0; }
+  return MSTOPO_OK;
+}
+
+mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out) {
+  if (!h || !out) return MSTOPO_INVALID_ARG;
+  CKA(cudaStreamSynchronize(h->s));
+  prof_collect(h->prof);
+  out->launches = g_launch_count.load();
+  for (int k = 0; k < 4; ++k) {
+    out->kernel_launches[k] = h->prof.n[k];
+    out->kernel_ms[k] = h->prof.ms[k];
+  }
   return MSTOPO_OK;
 }
 

@@ -169,3 +169,129 @@ __device__ void bt_solve(const T* __restrict__ Linv, const T* __restrict__ C, in
   }
   __syncthreads();
 }
+
+// ------------------------------------------------------------- bulk-copy (TMA) staging
+// The factor blocks are streamed into shared memory with one cp.async.bulk per block,
+// completion tracked by an mbarrier (transaction bytes).  Waits are bounded: after
+// BT_WAIT_LIMIT polls the wait gives up, records MSTOPO_TIMEOUT in *err and the solve
+// stops issuing work (the host reports the status).
+#define BT_WAIT_LIMIT (1u << 24)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < BT_WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Matrix m of the solve sequence: forward L0, C0, L1, C1, ..., L_{NL-1};
+// backward L_{NL-1}, C_{NL-2}, L_{NL-2}, ..., C0, L0.
+template <typename T>
+__device__ __forceinline__ const T* bt_seq(const T* Linv, const T* C, long long nn, int NL, int m) {
+  const int nf = 2 * NL - 1;
+  if (m < nf) return (m & 1) ? C + (long long)(m >> 1) * nn : Linv + (long long)(m >> 1) * nn;
+  const int b = m - nf;
+  return (b & 1) ? C + (long long)(NL - 2 - (b >> 1)) * nn : Linv + (long long)(NL - 1 - (b >> 1)) * nn;
+}
+
+// In-place solve like bt_solve, with the factor blocks streamed by bulk copies into NBUF
+// shared buffers (NBUF = 2: the next block loads while the current one is used).
+// bars: NBUF mbarriers in shared memory; err: global status word.
+template <typename T, int NBUF>
+__device__ void bt_solve_bulk(const T* __restrict__ Linv, const T* __restrict__ C, int nb, int NL,
+                              T* X, int R, T* stage, T* t0, T* t1, uint64_t* bars, int* err) {
+  const long long nn = (long long)nb * nb;
+  const int nv = nb * R;
+  const uint32_t bytes = (uint32_t)(nn * sizeof(T));
+  const int nseq = 2 * (2 * NL - 1);
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int b = 0; b < NBUF && b < nseq; ++b) {
+      mbar_expect_tx(&bars[b], bytes);
+      bulk_g2s(stage + b * nn, bt_seq(Linv, C, nn, NL, b), bytes, &bars[b]);
+    }
+  uint32_t phase[NBUF];
+  for (int b = 0; b < NBUF; ++b) phase[b] = 0;
+  int m = 0;   // position in the sequence
+  auto acquire = [&]() -> const T* {
+    const int b = m % NBUF;
+    if (threadIdx.x == 0 && !s_abort && !mbar_wait(&bars[b], phase[b])) {
+      s_abort = 1;
+      atomicExch(err, (int)MSTOPO_TIMEOUT);
+    }
+    phase[b] ^= 1u;
+    __syncthreads();
+    return stage + b * nn;
+  };
+  auto release = [&]() {   // every thread is done with block m: refill its buffer
+    __syncthreads();
+    const int b = m % NBUF;
+    if (threadIdx.x == 0 && !s_abort && m + NBUF < nseq) {
+      mbar_expect_tx(&bars[b], bytes);
+      bulk_g2s(stage + b * nn, bt_seq(Linv, C, nn, NL, m + NBUF), bytes, &bars[b]);
+    }
+    ++m;
+  };
+  for (int k = 0; k < NL; ++k) {
+    T* Xk = X + (long long)k * nv;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    __syncthreads();
+    if (k > 0) {
+      const T* M = acquire();
+      bt_gemm<T, false, false>(M, t1, t0, nb, R, true, T(-1));
+      release();
+    }
+    const T* M = acquire();
+    bt_gemm<T, false, true>(M, t0, t1, nb, R, false, T(1));
+    release();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+  }
+  for (int k = NL - 1; k >= 0; --k) {
+    T* Xk = X + (long long)k * nv;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    __syncthreads();
+    if (k + 1 < NL) {
+      const T* M = acquire();
+      bt_gemm<T, true, false>(M, t1, t0, nb, R, true, T(-1));
+      release();
+    }
+    const T* M = acquire();
+    bt_gemm<T, true, true>(M, t0, t1, nb, R, false, T(1));
+    release();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+  }
+  __syncthreads();
+}

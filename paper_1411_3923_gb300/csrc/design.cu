@@ -156,14 +156,14 @@ __global__ void k_check_finite(const double* __restrict__ x, long long n, int* f
 cudaError_t launch_filter(const double* rho, double* rho_tilde, double* wsum, int dx, int dy,
                           double rmin, int periodic, cudaStream_t s) {
   int R = (int)ceil(rmin);
-  k_filter<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(rho, rho_tilde, wsum, dx, dy, rmin, R, periodic);
+  note_launch(), k_filter<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(rho, rho_tilde, wsum, dx, dy, rmin, R, periodic);
   return cudaGetLastError();
 }
 
 cudaError_t launch_filter_T(const double* g, const double* wsum, double* out, int dx, int dy,
                             double rmin, int periodic, cudaStream_t s) {
   int R = (int)ceil(rmin);
-  k_filter_T<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(g, wsum, out, dx, dy, rmin, R, periodic);
+  note_launch(), k_filter_T<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(g, wsum, out, dx, dy, rmin, R, periodic);
   return cudaGetLastError();
 }
 
@@ -171,14 +171,14 @@ cudaError_t launch_project(const double* rho_tilde, double* rbar, double* drbar,
                            const double* etas, int n_eta, double beta, cudaStream_t s) {
   Etas et;
   for (int k = 0; k < MSTOPO_MAX_SYS; ++k) et.eta[k] = k < n_eta ? etas[k] : 0.0;
-  k_project<<<cdiv(n, 256), 256, 0, s>>>(rho_tilde, rbar, drbar, n, et, n_eta, beta);
+  note_launch(), k_project<<<cdiv(n, 256), 256, 0, s>>>(rho_tilde, rbar, drbar, n, et, n_eta, beta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_simp(const double* rbar, double* E64, float* E32, int nelx, int nely,
                         int dx, int dy, int periodic, int n_eta, int n_design,
                         double E0, double Emin, double penal, cudaStream_t s) {
-  k_simp<<<dim3(cdiv(nelx, 128), nely, n_eta), 128, 0, s>>>(rbar, E64, E32, nelx, nely, dx, dy,
+  note_launch(), k_simp<<<dim3(cdiv(nelx, 128), nely, n_eta), 128, 0, s>>>(rbar, E64, E32, nelx, nely, dx, dy,
                                                              periodic, n_design, E0, Emin, penal);
   return cudaGetLastError();
 }
@@ -192,7 +192,7 @@ cudaError_t launch_sensitivity(const double* u, long long u_stride, const double
   for (int k = 0; k < MSTOPO_MAX_SYS; ++k) wk.w[k] = k < n_eta ? w[k] : 0.0;
   K0Mat km;
   for (int q = 0; q < 64; ++q) km.k[q] = K0[q];
-  k_sensitivity<<<dim3(cdiv(nelx, 128), nely), 128, 0, s>>>(u, u_stride, rbar, drbar, n_eta, wk,
+  note_launch(), k_sensitivity<<<dim3(cdiv(nelx, 128), nely), 128, 0, s>>>(u, u_stride, rbar, drbar, n_eta, wk,
                                                             nelx, nely, dx, dy, periodic,
                                                             n_design, dE, penal, km, g_fine);
   return cudaGetLastError();
@@ -200,11 +200,11 @@ cudaError_t launch_sensitivity(const double* u, long long u_stride, const double
 
 cudaError_t launch_tile_sum(const double* g_fine, double* g_design, int nelx, int nely,
                             int dx, int dy, cudaStream_t s) {
-  k_tile_sum<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(g_fine, g_design, nelx, nely, dx, dy);
+  note_launch(), k_tile_sum<<<dim3(cdiv(dx, 128), dy), 128, 0, s>>>(g_fine, g_design, nelx, nely, dx, dy);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s) {
-  k_check_finite<<<304, 256, 0, s>>>(x, n, flag);
+  note_launch(), k_check_finite<<<304, 256, 0, s>>>(x, n, flag);
   return cudaGetLastError();
 }

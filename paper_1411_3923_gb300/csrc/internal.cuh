@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -12,6 +14,25 @@
 #define MSTOPO_MAX_SYS 4      // realisations solved together with one preconditioner
 #define MSTOPO_MAX_EIG 16     // eigenvectors kept per agglomerate
 #define MSTOPO_RED_BLOCKS 304 // CTAs of the fused reduction kernels (2 per SM of a GB300)
+
+// Every kernel launch of the library is counted (process-wide), see mstopo_get_stats.
+extern std::atomic<long long> g_launch_count;
+inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+
+// Optional per-kernel device timing with CUDA events on the launching stream.
+enum { PROF_PATCH = 0, PROF_MATVEC32 = 1, PROF_MATVEC64 = 2, PROF_COARSE = 3, PROF_N = 4 };
+struct Prof {
+  int on = 0;
+  struct Pend { int which; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pend> pend;
+  double ms[PROF_N] = {0, 0, 0, 0};
+  long long n[PROF_N] = {0, 0, 0, 0};
+};
+cudaEvent_t prof_begin(Prof& p, cudaStream_t s);
+void prof_end(Prof& p, int which, cudaEvent_t a, cudaStream_t s);
+void prof_collect(Prof& p);   // after a stream synchronisation
+void prof_free(Prof& p);
 
 // ---------------------------------------------------------------------------------------
 // Element stiffness of a unit square, unit E, plane stress, derived in closed form
@@ -99,7 +120,9 @@ struct Precond {
   int* d_grp_first = nullptr;
   int* d_grp_count = nullptr;
   int n_groups = 0;
-  // per-type patch factors (block tridiagonal by node rows): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
+  // per-type patch factors (block tridiagonal by node rows of the (2H+1)^2 agglomerate box,
+  // artificial-boundary nodes Dirichlet): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
+  uint8_t* d_pfree = nullptr;       // [T][NP*nbP] free DOFs of the patch box
   double* d_pLinv64 = nullptr; double* d_pC64 = nullptr;
   float* d_pLinv32 = nullptr;  float* d_pC32 = nullptr;
   // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
@@ -158,6 +181,7 @@ struct mstopo_handle {
   double* d_u_all = nullptr;        // [MAX_SYS][n_dof] last all-realisation solution
   double* d_f_all = nullptr;        // load used for it
   double* d_host_stage = nullptr;   // device staging for the host-pointer entry point
+  Prof prof;
 };
 
 // precond.cu

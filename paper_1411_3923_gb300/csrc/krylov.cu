@@ -64,21 +64,21 @@ __global__ void k_finish_sum(const double* __restrict__ partials, double* __rest
 
 cudaError_t launch_dot_partials(const double* a, const double* b, long long n, int nsys,
                                 long long stride, double* partials, cudaStream_t s) {
-  k_dot<double, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  note_launch(), k_dot<double, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_dot_partials_f32(const float* a, const float* b, long long n, int nsys,
                                     long long stride, double* partials, cudaStream_t s) {
-  k_dot<float, float><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  note_launch(), k_dot<float, float><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_dot_partials_mix(const float* a, const double* b, long long n, int nsys,
                                     long long stride, double* partials, cudaStream_t s) {
-  k_dot<float, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
+  note_launch(), k_dot<float, double><<<dim3(RB, nsys), RT, 0, s>>>(a, b, n, stride, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_finish_sum(const double* partials, int nsys, double* out, cudaStream_t s) {
-  k_finish_sum<<<nsys, RT, 0, s>>>(partials, out);
+  note_launch(), k_finish_sum<<<nsys, RT, 0, s>>>(partials, out);
   return cudaGetLastError();
 }
 
@@ -109,16 +109,16 @@ __global__ void k_mask_copy(const double* __restrict__ a, double* __restrict__ b
 }
 
 cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t s) {
-  k_d2f<<<608, 256, 0, s>>>(a, b, n);
+  note_launch(), k_d2f<<<608, 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t s) {
-  k_f2d<<<608, 256, 0, s>>>(a, b, n);
+  note_launch(), k_f2d<<<608, 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 cudaError_t launch_mask_copy(const double* a, double* b, const uint8_t* nmask, long long n_nodes,
                              int nsys, long long stride, cudaStream_t s) {
-  k_mask_copy<<<dim3(304, nsys), 256, 0, s>>>(a, b, nmask, n_nodes, stride);
+  note_launch(), k_mask_copy<<<dim3(304, nsys), 256, 0, s>>>(a, b, nmask, n_nodes, stride);
   return cudaGetLastError();
 }
 
@@ -141,6 +141,11 @@ __global__ void __launch_bounds__(RT) k_pupdate(const PT* __restrict__ z, PT* __
   z += blockIdx.y * stride;
   p += blockIdx.y * stride;
   const double beta = c.beta;
+  if (beta == 0.0) {   // (re)start: p = z (p may hold stale or uninitialised data)
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
+      p[i] = z[i];
+    return;
+  }
   for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
     p[i] = (PT)((double)z[i] + beta * (double)p[i]);
 }
@@ -312,9 +317,11 @@ void solver_free(Solver& sv) {
 static mstopo_status true_residual(mstopo_handle* h, int sys0, int nsys, double* rr_dev) {
   Solver& sv = h->sv;
   const long long n = sv.n;
+  cudaEvent_t pa = prof_begin(h->prof, h->s);
   CK(launch_matvec_f64(sv.x, sv.tmp, h->d_E64 + (long long)sys0 * h->n_el, h->d_nmask, h->nelx,
                        h->nely, h->st64, nsys, n, h->n_el, h->s));
-  k_residual<<<dim3(RB, nsys), RT, 0, h->s>>>(sv.f, sv.tmp, sv.r, sv.r32, n, n, sv.partials);
+  prof_end(h->prof, PROF_MATVEC64, pa, h->s);
+  note_launch(), k_residual<<<dim3(RB, nsys), RT, 0, h->s>>>(sv.f, sv.tmp, sv.r, sv.r32, n, n, sv.partials);
   CK(cudaGetLastError());
   CK(launch_finish_sum(sv.partials, nsys, rr_dev, h->s));
   return MSTOPO_OK;
@@ -339,15 +346,16 @@ static mstopo_status precond(mstopo_handle* h, int nsys) {
 mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
                         const double* u0, mstopo_solve_info* infos) {
   Solver& sv = h->sv;
+  mstopo_status st = solver_alloc(h);
+  if (st != MSTOPO_OK) return st;
   const long long n = sv.n;
   const bool mixed = h->p.precision != MSTOPO_FP64;
   const double tol2 = h->p.tol * h->p.tol;
-  mstopo_status st = solver_alloc(h);
-  if (st != MSTOPO_OK) return st;
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, h->s));
+  CK(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), h->s));   // device-wait timeout word
   // f (same load for every system), masked; x0
   for (int s = 0; s < nsys; ++s) CK(launch_mask_copy(f, sv.f + s * n, h->d_nmask, h->n_nodes, 1, n, h->s));
   CK(launch_mask_copy(u0, sv.x, h->d_nmask, h->n_nodes, nsys, n, h->s));
@@ -360,11 +368,11 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   double* vtmp = sv.partials + (size_t)MSTOPO_MAX_SYS * 3 * RB;   // small scratch [nsys]
   CK(launch_dot_partials(sv.f, sv.f, n, nsys, n, sv.partials, h->s));
   CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
-  k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 0, tol2);
+  note_launch(), k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 0, tol2);
   CK(cudaGetLastError());
   st = true_residual(h, sys0, nsys, vtmp);
   if (st != MSTOPO_OK) return st;
-  k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 1, tol2);
+  note_launch(), k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 1, tol2);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -394,38 +402,49 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
         else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));
         CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
       }
-      k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, restart);
+      note_launch(), k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, restart);
       CK(cudaGetLastError());
       restart = 0;
       if (mixed) {
-        k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
+        note_launch(), k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
         CK(cudaGetLastError());
+        cudaEvent_t pa = prof_begin(h->prof, h->s);
         CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
                              h->n_el, h->s));
-        k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
+        prof_end(h->prof, PROF_MATVEC32, pa, h->s);
+        note_launch(), k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
       } else {
-        k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
+        note_launch(), k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
         CK(cudaGetLastError());
+        cudaEvent_t pa = prof_begin(h->prof, h->s);
         CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
                              h->n_el, h->s));
-        k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
+        prof_end(h->prof, PROF_MATVEC64, pa, h->s);
+        note_launch(), k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
       }
       CK(cudaGetLastError());
-      k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
+      note_launch(), k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
       CK(cudaGetLastError());
       if (mixed)
-        k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
+        note_launch(), k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
                                                             sv.partials, sv.sc);
       else
-        k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
+        note_launch(), k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
                                                              n, sv.partials, sv.sc);
       CK(cudaGetLastError());
-      k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
+      note_launch(), k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
       CK(cudaGetLastError());
     }
     total_iters += chunk;
+    int werr = 0;
     CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(&werr, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
+    prof_collect(h->prof);
+    if (werr) {
+      for (int s = 0; s < nsys; ++s) { sv.h_sc[s].status = werr; sv.h_sc[s].active = 0; done[s] = 1; }
+      break;
+    }
     // host decisions: convergence candidates and reliable updates need the true residual
     bool need_true = false;
     for (int s = 0; s < nsys; ++s) {

@@ -176,7 +176,7 @@ cudaError_t launch_matvec_f32(const float* u, float* y, const float* E, const ui
                               int nelx, int nely, const StencilCoef<float>& c, int nsys,
                               long long vec_stride, long long e_stride, cudaStream_t s) {
   dim3 grid(cdiv(nelx + 1, MV_TX), cdiv(nely + 1, MV_TY), nsys);
-  k_matvec<float><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
+  note_launch(), k_matvec<float><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
   return cudaGetLastError();
 }
 
@@ -184,6 +184,6 @@ cudaError_t launch_matvec_f64(const double* u, double* y, const double* E, const
                               int nelx, int nely, const StencilCoef<double>& c, int nsys,
                               long long vec_stride, long long e_stride, cudaStream_t s) {
   dim3 grid(cdiv(nelx + 1, MV_TX), cdiv(nely + 1, MV_TY), nsys);
-  k_matvec<double><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
+  note_launch(), k_matvec<double><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
   return cudaGetLastError();
 }

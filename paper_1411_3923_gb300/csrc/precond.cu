@@ -81,19 +81,21 @@ __global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restri
 // node is in the mesh and not Dirichlet; other rows/columns are identity.
 struct BoxSpec { int ox, oy, N, ex0, ex1, ey0, ey1; };
 
+// The box is the agglomerate's (2H+1)^2 node box with lower-left node ((I-1)H, (J-1)H);
+// elements of the agglomerate only ([(I-1)H, (I+1)H) in each direction).  artificial = 1
+// (patch matrices): box-edge nodes strictly inside the mesh form the artificial boundary and
+// are Dirichlet; box-edge nodes on the mesh boundary keep the physical conditions.
 __global__ void k_assemble_box(const double* __restrict__ E, const uint8_t* __restrict__ nmask,
                                int nelx, int nely, const int* __restrict__ rep, int H, int ncx,
-                               int off, int elem_lo, int elem_hi, K0P K0, double* __restrict__ A,
+                               int artificial, K0P K0, double* __restrict__ A,
                                double* __restrict__ B, uint8_t* __restrict__ freeo) {
   // blockIdx.x = type, blockIdx.y = line
   const int type = blockIdx.x, line = blockIdx.y;
   const int ia = rep[type];
   const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-  const int N = 2 * H + 1 - 2 * off;
-  const int ox = (I - 1) * H + off, oy = (J - 1) * H + off;
-  // element window: [ (I-1)H + elem_lo, (I+1)H + elem_hi )
-  const int ex0 = (I - 1) * H + elem_lo, ex1 = (I + 1) * H + elem_hi;
-  const int ey0 = (J - 1) * H + elem_lo, ey1 = (J + 1) * H + elem_hi;
+  const int N = 2 * H + 1;
+  const int ox = (I - 1) * H, oy = (J - 1) * H;
+  const int ex0 = ox, ex1 = ox + 2 * H, ey0 = oy, ey1 = oy + 2 * H;
   const int nb = 2 * N;
   const long long nn = (long long)nb * nb;
   double* Ak = A + ((long long)type * N + line) * nn;
@@ -102,6 +104,9 @@ __global__ void k_assemble_box(const double* __restrict__ E, const uint8_t* __re
     int x = ox + a, y = oy + b;
     if (a < 0 || a >= N || b < 0 || b >= N) return false;
     if (x < 0 || x > nelx || y < 0 || y > nely) return false;
+    if (artificial && ((a == 0 && x > 0) || (a == N - 1 && x < nelx) || (b == 0 && y > 0) ||
+                       (b == N - 1 && y < nely)))
+      return false;
     return !((nmask[(long long)y * (nelx + 1) + x] >> c) & 1);
   };
   for (int r = threadIdx.x; r < nb; r += blockDim.x) {
@@ -278,6 +283,7 @@ struct EigArgs {
   double* X; double* Y; double* KY;        // [T][NL][nb][q]
   int q, kmax; double lam_thresh;
   double* lambda; int* kept; double* res; int* sweeps;
+  int* err;
   K0P K0;
 };
 
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
   double* theta = scr + 3 * q * q;         // q
   double* res = theta + q;                 // q
   __shared__ int s_done, s_fail;
+  __shared__ __align__(8) uint64_t s_bars[2];
   // D = diag(K_w) per DOF (from the assembled diagonal blocks)
   auto Dof = [&](long long dof) -> double {
     long long line = dof / nb, r = dof % nb;
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
     // Y = (K + s D)^-1 D X
     for (long long t = threadIdx.x; t < n * q; t += blockDim.x) Y[t] = Dof(t / q) * X[t] * fr[t / q];
     __syncthreads();
-    bt_solve<double, true>(Linv, C, nb, N, Y, q, stage, t0, t1);
+    bt_solve_bulk<double, 1>(Linv, C, nb, N, Y, q, stage, t0, t1, s_bars, a.err);
     for (long long t = threadIdx.x; t < n * q; t += blockDim.x) if (!fr[t / q]) Y[t] = 0.0;
     __syncthreads();
     box_apply(a, I, J, fr, Y, KY, q);
@@ -636,37 +643,41 @@ __global__ void __launch_bounds__(PC_THREADS) k_patch_solve(
     const T* __restrict__ r, long long stride, int nsys, int nelx, int nely, int H, int ncx,
     const int* __restrict__ grp_type, const int* __restrict__ grp_first,
     const int* __restrict__ grp_count, const int* __restrict__ perm,
-    const T* __restrict__ Linv, const T* __restrict__ C, T* __restrict__ Xg) {
+    const uint8_t* __restrict__ pfree, const T* __restrict__ Linv, const T* __restrict__ C,
+    T* __restrict__ Xg, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bars[2];
   extern __shared__ unsigned char smraw[];
   T* smem = reinterpret_cast<T*>(smraw);
   const int g = blockIdx.x;
   const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
-  const int N = 2 * H - 1, nb = 2 * N;
+  const int N = 2 * H + 1, nb = 2 * N;
+  const uint8_t* fr = pfree + (long long)type * N * nb;
   const int R = PC_GROUP * nsys;
   const long long nn = (long long)nb * nb;
   T* X = Xg + (long long)g * N * nb * R;
-  // gather: X[line][2a+c][p*nsys+s] = r_s(node) on the patch box (zero outside the mesh)
+  // gather: X[line][2a+c][p*nsys+s] = r_s(node) on the free DOFs of the patch box
   for (long long t = threadIdx.x; t < (long long)N * nb * R; t += blockDim.x) {
     const int col = t % R;
     const long long dof = t / R;
     const int p = col / nsys, s = col % nsys;
     T v = T(0);
-    if (p < cnt) {
+    if (p < cnt && fr[dof]) {
       const int ia = perm[first + p];
       const int I = ia % (ncx + 1), J = ia / (ncx + 1);
       const int line = dof / nb, rr = dof % nb;
-      const int x = (I - 1) * H + 1 + (rr >> 1), y = (J - 1) * H + 1 + line;
+      const int x = (I - 1) * H + (rr >> 1), y = (J - 1) * H + line;
       if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
         v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (rr & 1)];
     }
     X[t] = v;
   }
   __syncthreads();
+  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
   T* stage = smem;
-  T* t0 = stage + nn;
+  T* t0 = stage + NBUF * nn;
   T* t1 = t0 + nb * R;
-  bt_solve<T, true>(Linv + (long long)type * N * nn, C + (long long)type * (N - 1) * nn, nb, N, X,
-                    R, stage, t0, t1);
+  bt_solve_bulk<T, NBUF>(Linv + (long long)type * N * nn, C + (long long)type * (N - 1) * nn, nb, N,
+                         X, R, stage, t0, t1, bars, err);
 }
 
 // z(node) = sum over the (up to four) agglomerates around the node of
@@ -681,23 +692,23 @@ __global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nel
                           const uint8_t* __restrict__ nmask, int part) {
   const long long nn1 = (long long)(nelx + 1) * (nely + 1);
   const int s = blockIdx.y;
-  const int N = 2 * H + 1, NP = 2 * H - 1, nbP = 2 * NP;
+  const int N = 2 * H + 1, NP = N, nbP = 2 * NP;
   const int R = PC_GROUP * nsys;
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn1;
        node += (long long)gridDim.x * blockDim.x) {
     const int x = node % (nelx + 1), y = node / (nelx + 1);
     double zx = 0.0, zy = 0.0;
     const int Ib = x / H, Jb = y / H;
-    for (int dj = 0; dj < 2; ++dj)
-      for (int di = 0; di < 2; ++di) {
-        const int I = Ib + di, J = Jb + dj;
-        if (I > ncx || J > ncy) continue;
-        if (abs(x - I * H) >= H || abs(y - J * H) >= H) continue;
+    // agglomerates whose closed box contains the node: |x - IH| <= H, |y - JH| <= H.  chi
+    // vanishes on the box edge, and the patch solution vanishes on artificial edge nodes.
+    for (int J = max(Jb - 1, 0); J <= min(Jb + 1, ncy); ++J)
+      for (int I = max(Ib - 1, 0); I <= min(Ib + 1, ncx); ++I) {
+        if (abs(x - I * H) > H || abs(y - J * H) > H) continue;
         const int i = J * (ncx + 1) + I;
-        if (part != 2) {
+        const long long l = (long long)(y - (J - 1) * H) * N + (x - (I - 1) * H);
+        if (part != 2 && abs(x - I * H) < H && abs(y - J * H) < H) {
           const int t = type_of[i], k = kept[t];
           const double chi = hat(x, I * H, H) * hat(y, J * H, H);
-          const long long l = (long long)(y - (J - 1) * H) * N + (x - (I - 1) * H);
           const T* pp = psi + ((long long)t * N * N + l) * 2 * kmax;
           const double* u = uc + (long long)s * Nt + coff[i];
           double ax = 0.0, ay = 0.0;
@@ -709,8 +720,7 @@ __global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nel
           zy = fma(chi, ay, zy);
         }
         if (part != 1) {
-          const int la = x - (I - 1) * H - 1, lb = y - (J - 1) * H - 1;
-          const long long base = ((long long)agg_group[i] * NP + lb) * nbP + 2 * la;
+          const long long base = (long long)agg_group[i] * NP * nbP + 2 * l;
           const int col = agg_slot[i] * nsys + s;
           zx += (double)Xg[base * R + col];
           zy += (double)Xg[(base + 1) * R + col];
@@ -737,7 +747,7 @@ static void dfree(void* p) { if (p) cudaFree(p); }
 void precond_free(Precond& pc) {
   dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff); dfree(pc.d_perm);
   dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count);
-  dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
+  dfree(pc.d_pfree); dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
   dfree(pc.d_Kc); dfree(pc.d_Kcinv); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
   dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
@@ -755,7 +765,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   Precond& pc = h->pc;
   cudaStream_t s = h->s;
   const int H = h->p.H;
-  pc.H = H; pc.NA = 2 * H + 1; pc.NP = 2 * H - 1; pc.nbA = 2 * pc.NA; pc.nbP = 2 * pc.NP;
+  pc.H = H; pc.NA = 2 * H + 1; pc.NP = 2 * H + 1; pc.nbA = 2 * pc.NA; pc.nbP = 2 * pc.NP;
   pc.ncx = h->nelx / H; pc.ncy = h->nely / H; pc.Nc = (pc.ncx + 1) * (pc.ncy + 1);
   pc.kmax = h->p.n_eig;
   pc.local_shift = h->p.precision == MSTOPO_MIXED ? h->p.local_shift : 0.0;
@@ -769,7 +779,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   unsigned long long* d_hash;
   CKB(cudaMalloc(&d_hash, (size_t)pc.Nc * 16));
   CKB(cudaMemsetAsync(d_hash, 0, (size_t)pc.Nc * 16, s));
-  k_hash_agg<<<pc.Nc, PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, H, pc.ncx, d_hash);
+  note_launch(), k_hash_agg<<<pc.Nc, PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, H, pc.ncx, d_hash);
   CKB(cudaGetLastError());
   std::vector<unsigned long long> hh((size_t)pc.Nc * 2);
   CKB(cudaMemcpyAsync(hh.data(), d_hash, (size_t)pc.Nc * 16, cudaMemcpyDeviceToHost, s));
@@ -814,10 +824,10 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMalloc(&dX, (size_t)T * nA * q * 8));
   CKB(cudaMalloc(&dY, (size_t)T * nA * q * 8));
   CKB(cudaMalloc(&dKY, (size_t)T * nA * q * 8));
-  k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
-                                                    pc.ncx, 0, 0, 0, K0, dA, dB, dfree_);
+  note_launch(), k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
+                                                    pc.ncx, 0, K0, dA, dB, dfree_);
   CKB(cudaGetLastError());
-  k_bt_factor<<<T, PC_THREADS, 0, s>>>(dA, dB, dfree_, EIG_SHIFT, nbA, NA, dLi, dC, dS, d_st);
+  note_launch(), k_bt_factor<<<T, PC_THREADS, 0, s>>>(dA, dB, dfree_, EIG_SHIFT, nbA, NA, dLi, dC, dS, d_st);
   CKB(cudaGetLastError());
   CKB(cudaMalloc(&pc.d_lambda, (size_t)T * MSTOPO_MAX_EIG * 8));
   CKB(cudaMemsetAsync(pc.d_lambda, 0, (size_t)T * MSTOPO_MAX_EIG * 8, s));
@@ -830,15 +840,23 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   ea.X = dX; ea.Y = dY; ea.KY = dKY; ea.q = q; ea.kmax = pc.kmax; ea.lam_thresh = h->p.lambda_thresh;
   ea.lambda = pc.d_lambda; ea.kept = pc.d_kept; ea.res = pc.d_eigres; ea.sweeps = pc.d_eigsweeps;
   ea.K0 = K0;
+  ea.err = h->d_flag + 1;
   size_t esm = (size_t)(nnA + 2 * nbA * q + 6 * q * q + 2 * q) * 8;
   CKB(cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  k_eigen<<<T, PC_THREADS, esm, s>>>(ea);
+  CKB(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), s));
+  note_launch(), k_eigen<<<T, PC_THREADS, esm, s>>>(ea);
   CKB(cudaGetLastError());
   std::vector<int> fst(T);
   CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
   pc.h_kept.resize(T);
   CKB(cudaMemcpyAsync(pc.h_kept.data(), pc.d_kept, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  int werr = 0;
+  CKB(cudaMemcpyAsync(&werr, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CKB(cudaStreamSynchronize(s));
+  if (werr) {
+    h->err = "bounded device wait gave up in the eigen-solve";
+    return MSTOPO_TIMEOUT;
+  }
   for (int t = 0; t < T; ++t) {
     if (fst[t] || pc.h_kept[t] < 1) {
       h->err = "agglomerate eigenproblem failed (non-positive pivot or Rayleigh-Ritz breakdown)";
@@ -847,7 +865,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   }
   CKB(cudaMalloc(&pc.d_psi64, (size_t)T * nA * pc.kmax * 8));
   CKB(cudaMalloc(&pc.d_psi32, (size_t)T * nA * pc.kmax * 4));
-  k_store_psi<<<dim3(64, T), 256, 0, s>>>(dX, pc.d_kept, (int)nA, q, pc.kmax, pc.d_psi64, pc.d_psi32);
+  note_launch(), k_store_psi<<<dim3(64, T), 256, 0, s>>>(dX, pc.d_kept, (int)nA, q, pc.kmax, pc.d_psi64, pc.d_psi32);
   CKB(cudaGetLastError());
   CKB(cudaEventRecord(ev[2], s));
   cudaFree(dLi); cudaFree(dC); cudaFree(dS); cudaFree(dX); cudaFree(dY); cudaFree(dKY);
@@ -861,24 +879,24 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMalloc(&pA, (size_t)T * NP * nnP * 8));
   CKB(cudaMalloc(&pB, (size_t)T * (NP - 1) * nnP * 8));
   CKB(cudaMalloc(&pS, (size_t)T * nnP * 8));
-  CKB(cudaMalloc(&pfree, (size_t)T * nP));
+  CKB(cudaMalloc(&pc.d_pfree, (size_t)T * nP));
+  pfree = pc.d_pfree;
   CKB(cudaMalloc(&pc.d_pLinv64, (size_t)T * NP * nnP * 8));
   CKB(cudaMalloc(&pc.d_pC64, (size_t)T * (NP - 1) * nnP * 8));
-  // elements touching the inner nodes: the whole agglomerate (offset window 0)
-  k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
-                                                    pc.ncx, 1, 0, 0, K0, pA, pB, pfree);
+  note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
+                                                    pc.ncx, 1, K0, pA, pB, pfree);
   CKB(cudaGetLastError());
-  k_bt_factor<<<T, PC_THREADS, 0, s>>>(pA, pB, pfree, pc.local_shift, nbP, NP, pc.d_pLinv64,
+  note_launch(), k_bt_factor<<<T, PC_THREADS, 0, s>>>(pA, pB, pfree, pc.local_shift, nbP, NP, pc.d_pLinv64,
                                        pc.d_pC64, pS, d_st);
   CKB(cudaGetLastError());
   CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
   CKB(cudaMalloc(&pc.d_pLinv32, (size_t)T * NP * nnP * 4));
   CKB(cudaMalloc(&pc.d_pC32, (size_t)T * (NP - 1) * nnP * 4));
-  k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pLinv64, pc.d_pLinv32, (long long)T * NP * nnP);
-  k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pC64, pc.d_pC32, (long long)T * (NP - 1) * nnP);
+  note_launch(), k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pLinv64, pc.d_pLinv32, (long long)T * NP * nnP);
+  note_launch(), k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pC64, pc.d_pC32, (long long)T * (NP - 1) * nnP);
   CKB(cudaGetLastError());
   CKB(cudaStreamSynchronize(s));
-  cudaFree(pA); cudaFree(pB); cudaFree(pS); cudaFree(pfree); cudaFree(d_rep);
+  cudaFree(pA); cudaFree(pB); cudaFree(pS); cudaFree(d_rep);
   for (int t = 0; t < T; ++t)
     if (fst[t]) {
       h->err = "patch matrix not positive definite";
@@ -919,12 +937,12 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMalloc(&cS, (size_t)nnc * 8));
   CKB(cudaMemsetAsync(cA, 0, (size_t)NLc * nnc * 8, s));
   CKB(cudaMemsetAsync(cB, 0, (size_t)std::max(NLc - 1, 1) * nnc * 8, s));
-  k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(E, h->nelx, h->nely, H, pc.d_type_of_agg,
+  note_launch(), k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(E, h->nelx, h->nely, H, pc.d_type_of_agg,
                                                           pc.d_kept, pc.d_psi64, pc.kmax, K0, cm,
                                                           cA, cB, nbc);
   CKB(cudaGetLastError());
   // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
-  k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, nbc, NLc, cLi, cC, cS, d_st);
+  note_launch(), k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, nbc, NLc, cLi, cC, cS, d_st);
   CKB(cudaGetLastError());
   int cst = 0;
   CKB(cudaMemcpyAsync(&cst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -932,7 +950,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   const int nblk = cdiv((long long)NLc * nbc, RC);
   CKB(cudaMalloc(&cX, (size_t)nblk * NLc * nbc * RC * 8));
   CKB(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nbc * RC * 8));
-  k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi, cC, nbc, NLc, d_s2o, Nt, cX, pc.d_Kcinv);
+  note_launch(), k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi, cC, nbc, NLc, d_s2o, Nt, cX, pc.d_Kcinv);
   CKB(cudaGetLastError());
   CKB(cudaStreamSynchronize(s));
   cudaFree(cA); cudaFree(cB); cudaFree(cLi); cudaFree(cC); cudaFree(cS); cudaFree(cX); cudaFree(d_s2o);
@@ -1008,22 +1026,28 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int 
   cudaStream_t s = h->s;
   const long long n = h->n_dof;
   if (part != 2) {
-    k_restrict<T><<<dim3(pc.Nc, nsys), PC_THREADS, 0, s>>>(r, n, h->nelx, h->nely, pc.H, pc.ncx,
+    note_launch(), k_restrict<T><<<dim3(pc.Nc, nsys), PC_THREADS, 0, s>>>(r, n, h->nelx, h->nely, pc.H, pc.ncx,
                                                           pc.d_type_of_agg, pc.d_kept, pc.d_coff,
                                                           psi, pc.kmax, pc.d_rc, pc.Nt);
-    k_coarse_gemv<<<cdiv((long long)pc.Nt * 32, 256), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, nsys);
+    cudaEvent_t pa = prof_begin(h->prof, s);
+    note_launch(), k_coarse_gemv<<<cdiv((long long)pc.Nt * 32, 256), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, nsys);
+    prof_end(h->prof, PROF_COARSE, pa, s);
   }
   if (part != 1) {
     const int NP = pc.NP, nbP = pc.nbP, R = PC_GROUP * nsys;
-    size_t sm = ((size_t)nbP * nbP + 2 * (size_t)nbP * R) * sizeof(T);
+    const int nbuf = sizeof(T) == 4 ? 2 : 1;
+    size_t sm = ((size_t)nbuf * nbP * nbP + 2 * (size_t)nbP * R) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_patch_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_patch_solve<T><<<pc.n_groups, PC_THREADS, sm, s>>>(r, n, nsys, h->nelx, h->nely, pc.H, pc.ncx,
+    cudaEvent_t pa = prof_begin(h->prof, s);
+    note_launch(), k_patch_solve<T><<<pc.n_groups, PC_THREADS, sm, s>>>(r, n, nsys, h->nelx, h->nely, pc.H, pc.ncx,
                                                           pc.d_grp_type, pc.d_grp_first,
-                                                          pc.d_grp_count, pc.d_perm, Linv, C, Xg);
+                                                          pc.d_grp_count, pc.d_perm, pc.d_pfree, Linv, C, Xg,
+                                                          h->d_flag + 1);
+    prof_end(h->prof, PROF_PATCH, pa, s);
     (void)NP;
   }
-  k_combine<T><<<dim3(608, nsys), 256, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
+  note_launch(), k_combine<T><<<dim3(608, nsys), 256, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
                                                pc.d_uc, pc.Nt, agg_group_ptr(pc), agg_slot_ptr(pc), Xg,
                                                h->d_nmask, part);

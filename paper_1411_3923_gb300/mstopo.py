@@ -43,6 +43,14 @@ class _BuildInfo(C.Structure):
                 ("ms_total", C.c_float)]
 
 
+class _Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("kernel_launches", C.c_int64 * 4),
+                ("kernel_ms", C.c_double * 4)]
+
+
+KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
+
+
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("replacements", C.c_int32),
                 ("rel_residual", C.c_double), ("compliance", C.c_double), ("ms", C.c_float)]
@@ -54,7 +62,8 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_num_realisations", "mstopo_set_design", "mstopo_get_field",
            "mstopo_build_preconditioner", "mstopo_solve", "mstopo_solve_host",
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
-           "mstopo_apply_precond", "mstopo_get_eigenpairs"]
+           "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
+           "mstopo_get_stats"]
 
 
 def load(path: str = LIB_PATH):
@@ -83,6 +92,8 @@ def load(path: str = LIB_PATH):
         "mstopo_apply_K_f32": ([vp, i32, vp, vp], i32),
         "mstopo_apply_precond": ([vp, i32, i32, vp, vp], i32),
         "mstopo_get_eigenpairs": ([vp, i32, i32, vp, vp, vp], i32),
+        "mstopo_set_profiling": ([vp, i32], i32),
+        "mstopo_get_stats": ([vp, C.POINTER(_Stats)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -183,7 +194,8 @@ class Problem:
         u0p = _ptr(_dev(u0)) if u0 is not None else None
         st = _lib.mstopo_solve(self._h, realisation, _ptr(f), _ptr(u), u0p, infos)
         out = [{k: getattr(i, k) for k, _ in _SolveInfo._fields_} for i in infos]
-        self._check(st)
+        if st != 0:
+            raise MstopoError(st, _lib.mstopo_last_error(self._h).decode() + f" {out}")
         return u, out
 
     def solve_host(self, f: np.ndarray, realisation: int = -1, u: Optional[np.ndarray] = None,
@@ -234,6 +246,27 @@ class Problem:
         self._check(_lib.mstopo_get_eigenpairs(self._h, I, J, lam.ctypes.data, psi.ctypes.data,
                                                C.addressof(k)))
         return lam[:k.value], psi[..., :k.value], k.value
+
+
+def _stats_dict(st: "_Stats") -> dict:
+    out = {"launches": st.launches}
+    for name, k in KERNEL_IDS.items():
+        out[name] = {"launches": st.kernel_launches[k], "ms": st.kernel_ms[k]}
+    return out
+
+
+def _problem_stats(self) -> dict:
+    st = _Stats()
+    self._check(_lib.mstopo_get_stats(self._h, C.byref(st)))
+    return _stats_dict(st)
+
+
+def _problem_set_profiling(self, on: bool = True):
+    self._check(_lib.mstopo_set_profiling(self._h, 1 if on else 0))
+
+
+Problem.stats = _problem_stats
+Problem.set_profiling = _problem_set_profiling
 
 
 class RobustCompliance(torch.autograd.Function):
