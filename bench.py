@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Benchmark: PCG time to relative residual 1e-8, mixed precision vs FP64, on one GB300.
+
+One step = one pass of the whole hot path on the 1024x512 MBB workload (1,051,650 DOFs,
+periodic Bernoulli(0.4) 32x32 cell, filter radius 3, beta 8, coarse cells H = 32 with 6
+eigenvectors): density filter + projection + SIMP, preconditioner build (agglomerate
+de-duplication, local eigen-solves, coarse matrix, patch factors), MIXED flexible CG to a
+true FP64 relative residual of 1e-8, compliance and design sensitivity.  Inputs are
+resident in HBM; L2 is flushed (256 MiB write) before every timed step.
+
+value        = mean device time of the MIXED solve (PCG to 1e-8), ms
+fp64         = the same solve with the FP64 method on the same inputs
+matvec       = FP32 matrix-free matvec on the 3200x4096 mesh (26.2M DOFs, inputs > L2)
+roofline     = the dominant kernel of the step (event-timed inside this run)
+cpu_baseline = the FP64 CPU oracle on a bounded sample of the same workload
+e2e          = the MIXED solve through mstopo_solve_host (pinned host f and u, copies timed)
+
+--impl reference times the CPU oracle (the reference arm of this build) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time to 1e-8 rel. residual & matvec GB/s, mixed vs FP64, up to 26M DOFs"
+WORKLOAD = "mbb_c2"
+WORKLOAD_DESC = ("MBB beam 1024x512 Q4 (1,051,650 DOFs), periodic 32x32 Bernoulli(0.4) void cell, "
+                 "rmin 3, beta 8, eta 0.5, E0/Emin 1e9, p 3, H 32, 6 eigenvectors, tol 1e-8")
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak: 152 SMs x 2 FP64 FMA/clk (measured 1.19 TFLOP/s at ~1.95 GHz) x 2 x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "source": "measured"}
+    except Exception:
+        return {**PEAKS_FALLBACK, "source": "fallback"}
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.device_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------ CPU oracle
+def oracle_sample(scale: int, with_build_time: bool = False) -> dict:
+    """Run the FP64 oracle's two-level PCG on a 1/scale copy of the workload (same cell,
+    same H and basis size) in a fresh process limited to one BLAS thread."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads
+from oracle import pipeline, msfem
+wl = workloads.make({WORKLOAD!r}, scale={scale})
+grid, K0, prob, chain = pipeline.build(wl)
+t0 = time.perf_counter()
+fw = chain.forward(wl.rho)
+tl = msfem.TwoLevel(prob, fw["E"][0], wl.H, wl.n_eig)
+t1 = time.perf_counter()
+Kf = prob.free_matrix(fw["E"][0])
+f = grid.nodal_from_neutral(wl.force)[prob.free]
+t2 = time.perf_counter()
+x, it, rr = msfem.pcg(Kf, f, tl.apply, tol=wl.tol)
+t3 = time.perf_counter()
+print(json.dumps({{"build_s": t1 - t0, "solve_s": t3 - t2, "iterations": it, "rel_residual": rr,
+                   "dofs": grid.n_dof, "nelx": wl.nelx, "nely": wl.nely}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(full_dofs: int, scale: int = 8) -> dict:
+    s = oracle_sample(scale)
+    ms_full = s["solve_s"] * 1e3 * full_dofs / s["dofs"]
+    return {"value": ms_full, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle two-level PCG to 1e-8 on the {s['nelx']}x{s['nely']} copy of the "
+                       f"workload ({s['dofs']} DOFs, same cell, H and basis size): "
+                       f"{s['solve_s']:.2f} s, {s['iterations']} iterations, scaled by DOFs to "
+                       f"{full_dofs}; build {s['build_s']:.1f} s not included; SuperLU and NumPy "
+                       f"on one thread")}
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args, rank: int, world: int):
+    import numpy as np
+    import torch
+
+    import paper_1411_3923_gb300 as m
+    import workloads
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    peaks = load_peaks()
+    wl = workloads.make(WORKLOAD)
+    rho = torch.from_numpy(wl.rho).to(dev)
+    f = torch.from_numpy(wl.force).to(dev)
+
+    def problem(prec):
+        return m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
+                         penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=wl.tol,
+                         max_iter=5000)
+
+    mixed, fp64 = problem("mixed"), problem("fp64")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(prob, ev):
+        ev[0].record()
+        prob.set_design(rho, wl.rmin, wl.beta, wl.etas, wl.cell)
+        ev[1].record()
+        binfo = prob.build_preconditioner(-1)
+        ev[2].record()
+        _, infos = prob.solve(f, -1)
+        ev[3].record()
+        c, fr, g = prob.compliance_and_sensitivity(1.0)
+        ev[4].record()
+        return binfo, infos, c
+
+    def new_events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    for _ in range(args.warmup):
+        step(mixed, new_events())
+        step(fp64, new_events())
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps of the MIXED path ----
+    mixed.set_profiling(True)
+    launches0 = mixed.stats()["launches"]
+    dev_id = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(
+        torch.cuda.get_device_properties(dev), "uuid") else str(dev.index)
+    if dev_id and not dev_id.startswith("GPU-") and len(dev_id) > 8:
+        dev_id = "GPU-" + dev_id
+    sampler = ClockSampler(dev_id)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    per = []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev = new_events()
+        binfo, infos, c = step(mixed, ev)
+        torch.cuda.synchronize()
+        per.append({"design": ev[0].elapsed_time(ev[1]), "build": ev[1].elapsed_time(ev[2]),
+                    "solve": ev[2].elapsed_time(ev[3]), "sens": ev[3].elapsed_time(ev[4]),
+                    "step": ev[0].elapsed_time(ev[4]), "iters": [i["iterations"] for i in infos],
+                    "res": [i["rel_residual"] for i in infos]})
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    st = mixed.stats()
+    launches = st["launches"] - launches0
+    mixed.set_profiling(False)
+
+    solve_ms = statistics.mean(p["solve"] for p in per)
+    step_ms = statistics.mean(p["step"] for p in per)
+
+    # ---- FP64 method on the same inputs (same step, FP64 solve) ----
+    per64 = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev = new_events()
+        _, infos64, c64 = step(fp64, ev)
+        torch.cuda.synchronize()
+        per64.append({"solve": ev[2].elapsed_time(ev[3]), "iters": [i["iterations"] for i in infos64]})
+    fp64_ms = statistics.mean(p["solve"] for p in per64)
+
+    # ---- roofline of the dominant profiled kernel in the mixed step ----
+    kern = {k: v for k, v in st.items() if isinstance(v, dict)}
+    nsteps = args.steps
+    wl_N = 2 * wl.H + 1
+    nb = 2 * wl_N
+    n_agg = (wl.nelx // wl.H + 1) * (wl.nely // wl.H + 1)
+    n_iter_total = sum(sum(p["iters"]) for p in per)
+    # algorithmic work per launch
+    nodes = (wl.nelx + 1) * (wl.nely + 1)
+    patch_flops = 6.0 * wl_N * nb * nb * n_agg * len(wl.etas)        # 2 sweeps x (Linv/2 + C) per column
+    mv_bytes = nodes * 8 * 2 + wl.nelx * wl.nely * 4 + nodes          # u, y (float2), E, mask
+    cand = []
+    if kern["patch_solve"]["launches"]:
+        t = kern["patch_solve"]["ms"] / kern["patch_solve"]["launches"]
+        ach = patch_flops / (t * 1e-3) / 1e12
+        cand.append((kern["patch_solve"]["ms"], {
+            "kernel": "k_patch_solve<float>", "bound": "alu", "achieved": ach,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+            "traffic": None, "avg_launch_ms": t,
+            "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz"}))
+    if kern["matvec_f32"]["launches"]:
+        t = kern["matvec_f32"]["ms"] / kern["matvec_f32"]["launches"]
+        ach = mv_bytes / (t * 1e-3) / 1e9
+        cand.append((kern["matvec_f32"]["ms"], {
+            "kernel": "k_matvec<float>", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "avg_launch_ms": t}))
+    cand.sort(key=lambda x: -x[0])
+    roofline = cand[0][1] if cand else None
+    shares = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / nsteps} for k, v in kern.items()}
+
+    # ---- FP32 matvec on the 26.2M-DOF mesh (inputs larger than L2) ----
+    mv = None
+    if not args.skip_big_matvec:
+        big = workloads.make("mbb_c5")
+        pb = m.Problem(big.nelx, big.nely, big.fixed, nu=big.nu, E0=big.E0, Emin=big.Emin,
+                       penal=big.penal, H=big.H, n_eig=big.n_eig, precision="mixed")
+        pb.set_design(torch.from_numpy(big.rho).to(dev), big.rmin, big.beta, big.etas[:1], big.cell)
+        nb_nodes = (big.nelx + 1) * (big.nely + 1)
+        u32 = torch.randn(2 * nb_nodes, device=dev, dtype=torch.float32)
+        y32 = torch.empty_like(u32)
+        for _ in range(5):
+            pb.apply_K_f32(u32, 0, y32)
+        pb.set_profiling(True)
+        reps = 20
+        for _ in range(reps):
+            flush.zero_()
+            pb.apply_K_f32(u32, 0, y32)
+        sb = pb.stats()
+        pb.set_profiling(False)
+        t = sb["matvec_f32"]["ms"] / max(sb["matvec_f32"]["launches"], 1)
+        byts = nb_nodes * 8 * 2 + big.nelx * big.nely * 4 + nb_nodes
+        gbs = byts / (t * 1e-3) / 1e9
+        mv = {"mesh": f"{big.nelx}x{big.nely}", "dofs": 2 * nb_nodes, "avg_launch_ms": t,
+              "algorithmic_bytes": byts, "gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+              "frac": gbs / peaks["hbm_gbs"],
+              "bytes_per_node": "u 8 + y 8 (float2) + E 4/element + mask 1"}
+        pb.close()
+        del u32, y32
+
+    # ---- e2e through the host-pointer entry point (pinned buffers, copies timed) ----
+    fh = torch.from_numpy(wl.force).pin_memory()
+    uh = torch.empty((len(wl.etas), wl.nely + 1, wl.nelx + 1, 2), dtype=torch.float64).pin_memory()
+    mixed.set_design(rho, wl.rmin, wl.beta, wl.etas, wl.cell)
+    mixed.build_preconditioner(-1)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mixed.solve_host(fh.numpy(), -1, u=uh.numpy())
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": fh.numel() * 8,
+           "d2h_bytes_per_step": uh.numel() * 8,
+           "api": "mstopo_solve_host (pinned host f in, u out)"}
+
+    # ---- max over ranks ----
+    vals = torch.tensor([solve_ms, step_ms, fp64_ms, e2e["value"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    solve_ms, step_ms, fp64_ms, e2e_v = vals.tolist()
+    e2e["value"] = e2e_v
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": solve_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "dofs": 2 * nodes, "realisations": len(wl.etas),
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": fp64_ms, "unit": "ms", "iterations": per64[-1]["iters"],
+                 "speedup_mixed_vs_fp64": fp64_ms / solve_ms},
+        "mixed": {"iterations": per[-1]["iters"], "rel_residual": per[-1]["res"],
+                  "phases_ms": {k: statistics.mean(p[k] for p in per)
+                                for k in ("design", "build", "solve", "sens")},
+                  "build": binfo},
+        "matvec": mv, "roofline": roofline, "kernels": shares, "gpu_launches": launches,
+        "clocks": clocks, "e2e": e2e, "wall_s_timed": t_wall, "peaks": peaks,
+    }
+    if not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(2 * nodes, scale=args.cpu_scale)
+    return out
+
+
+def run_reference(args, rank: int, world: int):
+    """The reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    if rank != 0:
+        return None
+    import workloads
+    wl = workloads.make(WORKLOAD)
+    full = wl.n_dof
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(args.cpu_scale)
+    vals, samples = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = oracle_sample(args.cpu_scale)
+        samples.append(s)
+        vals.append(s["solve_s"] * 1e3 * full / s["dofs"])
+    v = statistics.mean(vals)
+    s = samples[-1]
+    sample = (f"oracle two-level PCG to 1e-8 on the {s['nelx']}x{s['nely']} copy of the workload "
+              f"({s['dofs']} DOFs), {s['iterations']} iterations, scaled by DOFs to {full}")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "dofs": full, "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+
+
+def run_only(args):
+    """One kernel in a short loop: 'patch' = FP32 patch solves of the 1024x512 workload's
+    preconditioner (apply_precond, MIXED, patches only); 'matvec' = FP32 matvec on the
+    3200x4096 mesh (26.2M DOFs)."""
+    import torch
+    import paper_1411_3923_gb300 as m
+    import workloads
+    dev = torch.device("cuda", 0)
+    name = WORKLOAD if args.only == "patch" else "mbb_c5"
+    wl = workloads.make(name)
+    prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
+                     penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision="mixed")
+    prob.set_design(torch.from_numpy(wl.rho).to(dev), wl.rmin, wl.beta, wl.etas[:1], wl.cell)
+    if args.only == "patch":
+        prob.build_preconditioner(-1)
+        r = torch.randn((wl.nely + 1, wl.nelx + 1, 2), dtype=torch.float64, device=dev)
+        for _ in range(args.reps):
+            prob.apply_precond(r, m.MIXED, 2)
+    else:
+        n = prob.n_dof
+        u = torch.randn(n, device=dev, dtype=torch.float32)
+        y = torch.empty_like(u)
+        for _ in range(args.reps):
+            prob.apply_K_f32(u, 0, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "workload": name, "reps": args.reps, "ok": True}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-scale", type=int, default=8)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-big-matvec", action="store_true")
+    ap.add_argument("--only", choices=["patch", "matvec"], default=None,
+                    help="run one kernel in a short loop (for ncu captures) and exit")
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.only:
+        run_only(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

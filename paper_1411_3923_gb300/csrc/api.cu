@@ -344,8 +344,10 @@ mstopo_status mstopo_apply_K_f32(mstopo_handle* h, int32_t realisation, const fl
   if (!h->design_ready) { h->err = "no design set"; return MSTOPO_NOT_READY; }
   CHECK_ARG(u && y, "null pointer");
   CHECK_ARG(realisation >= 0 && realisation < h->n_eta, "realisation out of range");
+  cudaEvent_t pa = prof_begin(h->prof, h->s);
   CKA(launch_matvec_f32(u, y, h->d_E32 + realisation * h->n_el, h->d_nmask, h->nelx, h->nely,
                         h->st32, 1, h->n_dof, h->n_el, h->s));
+  prof_end(h->prof, PROF_MATVEC32, pa, h->s);
   CKA(cudaStreamSynchronize(h->s));
   return MSTOPO_OK;
 }

@@ -211,6 +211,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Register-blocked variant for a compile-time number of right-hand sides R: two threads per
+// output row split the reduction range and combine with one shuffle; each thread keeps R
+// independent accumulators (R-way ILP) and reads each matrix entry once.
+template <typename T, bool TRANS, bool LOWER, int R>
+__device__ __forceinline__ void bt_gemm_rb(const T* M, const T* v, T* out, int nb,
+                                           bool accumulate, T sign) {
+  const int rows_per_pass = blockDim.x >> 1;
+  for (int base = 0; base < nb; base += rows_per_pass) {
+    const int i = base + (threadIdx.x >> 1), half = threadIdx.x & 1;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    if (i < nb) {
+      int c0 = 0, c1 = nb;
+      if (LOWER) {
+        if (TRANS) c0 = i;
+        else c1 = i + 1;
+      }
+      const int mid = (c0 + c1) >> 1;
+      const int cb = half ? mid : c0, ce = half ? c1 : mid;
+#pragma unroll 4
+      for (int c = cb; c < ce; ++c) {
+        const T m = TRANS ? M[c * nb + i] : M[i * nb + c];
+        const T* vc = v + c * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = fma(m, vc[r], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+    if (i < nb && !half) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        out[i * R + r] = accumulate ? fma(sign, acc[r], out[i * R + r]) : sign * acc[r];
+    }
+  }
+}
+
 // Matrix m of the solve sequence: forward L0, C0, L1, C1, ..., L_{NL-1};
 // backward L_{NL-1}, C_{NL-2}, L_{NL-2}, ..., C0, L0.
 template <typename T>
@@ -224,9 +262,11 @@ __device__ __forceinline__ const T* bt_seq(const T* Linv, const T* C, long long 
 // In-place solve like bt_solve, with the factor blocks streamed by bulk copies into NBUF
 // shared buffers (NBUF = 2: the next block loads while the current one is used).
 // bars: NBUF mbarriers in shared memory; err: global status word.
-template <typename T, int NBUF>
+// X layout: DOF_FAST = false -> [NL][nb][R] (right-hand sides fastest);
+//           DOF_FAST = true  -> [NL][R][nb] (DOFs fastest, coalesced gathers and scatters).
+template <typename T, int NBUF, int R, bool DOF_FAST>
 __device__ void bt_solve_bulk(const T* __restrict__ Linv, const T* __restrict__ C, int nb, int NL,
-                              T* X, int R, T* stage, T* t0, T* t1, uint64_t* bars, int* err) {
+                              T* X, T* stage, T* t0, T* t1, uint64_t* bars, int* err) {
   const long long nn = (long long)nb * nb;
   const int nv = nb * R;
   const uint32_t bytes = (uint32_t)(nn * sizeof(T));
@@ -264,34 +304,46 @@ __device__ void bt_solve_bulk(const T* __restrict__ Linv, const T* __restrict__ 
     }
     ++m;
   };
+  auto load = [&](const T* Xk) {
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+      if (DOF_FAST) t0[(q % nb) * R + q / nb] = Xk[q];
+      else t0[q] = Xk[q];
+    }
+  };
+  auto store = [&](T* Xk) {
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+      if (DOF_FAST) Xk[q] = t1[(q % nb) * R + q / nb];
+      else Xk[q] = t1[q];
+    }
+  };
   for (int k = 0; k < NL; ++k) {
     T* Xk = X + (long long)k * nv;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    load(Xk);
     __syncthreads();
     if (k > 0) {
       const T* M = acquire();
-      bt_gemm<T, false, false>(M, t1, t0, nb, R, true, T(-1));
+      bt_gemm_rb<T, false, false, R>(M, t1, t0, nb, true, T(-1));
       release();
     }
     const T* M = acquire();
-    bt_gemm<T, false, true>(M, t0, t1, nb, R, false, T(1));
+    bt_gemm_rb<T, false, true, R>(M, t0, t1, nb, false, T(1));
     release();
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+    store(Xk);
   }
   for (int k = NL - 1; k >= 0; --k) {
     T* Xk = X + (long long)k * nv;
     __syncthreads();
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) t0[q] = Xk[q];
+    load(Xk);
     __syncthreads();
     if (k + 1 < NL) {
       const T* M = acquire();
-      bt_gemm<T, true, false>(M, t1, t0, nb, R, true, T(-1));
+      bt_gemm_rb<T, true, false, R>(M, t1, t0, nb, true, T(-1));
       release();
     }
     const T* M = acquire();
-    bt_gemm<T, true, true>(M, t0, t1, nb, R, false, T(1));
+    bt_gemm_rb<T, true, true, R>(M, t0, t1, nb, false, T(1));
     release();
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) Xk[q] = t1[q];
+    store(Xk);
   }
   __syncthreads();
 }

@@ -32,6 +32,7 @@
 #include "blocktri.cuh"
 
 #define PC_THREADS 256
+#define SOLVE_THREADS 320   // 160 rows x 2 threads per pass covers nb = 2(2H+1) up to H = 39
 #define PC_GROUP 4          // patches of one type solved together per CTA (x systems)
 #define EIG_MAX_SWEEPS 80
 #define EIG_TOL 1e-7
@@ -320,10 +321,12 @@ __device__ void box_apply(const EigArgs& a, int I, int J, const uint8_t* freem, 
   }
 }
 
-__global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
+template <int Q>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
   extern __shared__ double smem[];
   const int type = blockIdx.x;
-  const int H = a.H, N = 2 * H + 1, nb = 2 * N, q = a.q;
+  const int H = a.H, N = 2 * H + 1, nb = 2 * N;
+  constexpr int q = Q;
   const long long n = (long long)N * nb, nn = (long long)nb * nb;
   const int ia = a.rep[type];
   const int I = ia % (a.ncx + 1), J = ia / (a.ncx + 1);
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
     // Y = (K + s D)^-1 D X
     for (long long t = threadIdx.x; t < n * q; t += blockDim.x) Y[t] = Dof(t / q) * X[t] * fr[t / q];
     __syncthreads();
-    bt_solve_bulk<double, 1>(Linv, C, nb, N, Y, q, stage, t0, t1, s_bars, a.err);
+    bt_solve_bulk<double, 1, Q, false>(Linv, C, nb, N, Y, stage, t0, t1, s_bars, a.err);
     for (long long t = threadIdx.x; t < n * q; t += blockDim.x) if (!fr[t / q]) Y[t] = 0.0;
     __syncthreads();
     box_apply(a, I, J, fr, Y, KY, q);
@@ -439,6 +442,26 @@ __global__ void __launch_bounds__(PC_THREADS) k_eigen(EigArgs a) {
     a.kept[type] = s_fail ? -1 : kept;
     a.res[type] = m;
     a.sweeps[type] = sweep;
+  }
+}
+
+template <int Q>
+static cudaError_t launch_eigen_q(int T, size_t esm, cudaStream_t s, const EigArgs& ea) {
+  cudaError_t e = cudaFuncSetAttribute(k_eigen<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_eigen<Q><<<T, SOLVE_THREADS, esm, s>>>(ea);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_eigen(int q, int T, size_t esm, cudaStream_t s, const EigArgs& ea) {
+  switch (q) {
+    case 8: return launch_eigen_q<8>(T, esm, s, ea);
+    case 12: return launch_eigen_q<12>(T, esm, s, ea);
+    case 16: return launch_eigen_q<16>(T, esm, s, ea);
+    case 20: return launch_eigen_q<20>(T, esm, s, ea);
+    case 24: return launch_eigen_q<24>(T, esm, s, ea);
+    case 28: return launch_eigen_q<28>(T, esm, s, ea);
+    default: return launch_eigen_q<32>(T, esm, s, ea);
   }
 }
 
@@ -578,6 +601,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_inverse(
 
 // ------------------------------------------------------------------------------ apply
 // rc[s][coff[i] + a] = sum over the agglomerate box nodes of chi_i psi_a . r
+// chi_i = (H - |x - IH|)(H - |y - JH|) / H^2 (the bilinear hat, integer numerator).
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_restrict(
     const T* __restrict__ r, long long stride, int nelx, int nely, int H, int ncx,
@@ -588,9 +612,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_restrict(
   const int I = i % (ncx + 1), J = i / (ncx + 1);
   const int t = type_of[i], k = kept[t];
   const int N = 2 * H + 1;
+  const T invH2 = T(1) / (T)(H * H);
   const T* P = psi + (long long)t * N * N * 2 * kmax;
   r += s * stride;
   T acc[MSTOPO_MAX_EIG];
+#pragma unroll
   for (int a = 0; a < MSTOPO_MAX_EIG; ++a) acc[a] = T(0);
   // nodes with chi > 0: strictly inside the box
   const int M = N - 2;
@@ -598,17 +624,22 @@ __global__ void __launch_bounds__(PC_THREADS) k_restrict(
     const int la = 1 + u % M, lb = 1 + u / M;
     const int x = (I - 1) * H + la, y = (J - 1) * H + lb;
     if (x < 0 || x > nelx || y < 0 || y > nely) continue;
-    const T chi = (T)(hat(x, I * H, H) * hat(y, J * H, H));
+    const T chi = (T)((H - abs(la - H)) * (H - abs(lb - H))) * invH2;
     const long long node = (long long)y * (nelx + 1) + x;
     const T rx = chi * r[2 * node], ry = chi * r[2 * node + 1];
     const T* pp = P + ((long long)lb * N + la) * 2 * kmax;
-    for (int a = 0; a < k; ++a) acc[a] = fma(rx, pp[a], fma(ry, pp[kmax + a], acc[a]));
+#pragma unroll
+    for (int a = 0; a < MSTOPO_MAX_EIG; ++a)
+      if (a < k) acc[a] = fma(rx, pp[a], fma(ry, pp[kmax + a], acc[a]));
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int a = 0; a < k; ++a) {
-    double v = (double)acc[a];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w][a] = v;
+#pragma unroll
+  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) {
+    if (a < k) {
+      double v = (double)acc[a];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[w][a] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < k) {
@@ -637,34 +668,34 @@ __global__ void k_coarse_gemv(const double* __restrict__ Kinv, const double* __r
 }
 
 // Patch solves: one CTA per group of up to PC_GROUP agglomerates of one type, all systems.
-// Right-hand side columns: slot = g * nsys + s.  Work buffer Xg [group][NP][nbP][R].
-template <typename T>
-__global__ void __launch_bounds__(PC_THREADS) k_patch_solve(
+// Right-hand side columns: slot = g * nsys + s (R = PC_GROUP * nsys of them).
+// Work buffer Xg [group][line][R][nbP] (DOFs fastest).
+template <typename T, int R>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_patch_solve(
     const T* __restrict__ r, long long stride, int nsys, int nelx, int nely, int H, int ncx,
     const int* __restrict__ grp_type, const int* __restrict__ grp_first,
     const int* __restrict__ grp_count, const int* __restrict__ perm,
     const uint8_t* __restrict__ pfree, const T* __restrict__ Linv, const T* __restrict__ C,
     T* __restrict__ Xg, int* __restrict__ err) {
   __shared__ __align__(8) uint64_t bars[2];
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   T* smem = reinterpret_cast<T*>(smraw);
   const int g = blockIdx.x;
   const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
   const int N = 2 * H + 1, nb = 2 * N;
   const uint8_t* fr = pfree + (long long)type * N * nb;
-  const int R = PC_GROUP * nsys;
   const long long nn = (long long)nb * nb;
   T* X = Xg + (long long)g * N * nb * R;
-  // gather: X[line][2a+c][p*nsys+s] = r_s(node) on the free DOFs of the patch box
+  // gather: X[line][p*nsys+s][2a+c] = r_s(node) on the free DOFs of the patch box
   for (long long t = threadIdx.x; t < (long long)N * nb * R; t += blockDim.x) {
-    const int col = t % R;
-    const long long dof = t / R;
+    const int rr = t % nb;
+    const int col = (t / nb) % R;
+    const int line = t / ((long long)nb * R);
     const int p = col / nsys, s = col % nsys;
     T v = T(0);
-    if (p < cnt && fr[dof]) {
+    if (p < cnt && fr[(long long)line * nb + rr]) {
       const int ia = perm[first + p];
       const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-      const int line = dof / nb, rr = dof % nb;
       const int x = (I - 1) * H + (rr >> 1), y = (J - 1) * H + line;
       if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
         v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (rr & 1)];
@@ -676,8 +707,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_patch_solve(
   T* stage = smem;
   T* t0 = stage + NBUF * nn;
   T* t1 = t0 + nb * R;
-  bt_solve_bulk<T, NBUF>(Linv + (long long)type * N * nn, C + (long long)type * (N - 1) * nn, nb, N,
-                         X, R, stage, t0, t1, bars, err);
+  bt_solve_bulk<T, NBUF, R, true>(Linv + (long long)type * N * nn,
+                                  C + (long long)type * (N - 1) * nn, nb, N, X, stage, t0, t1,
+                                  bars, err);
 }
 
 // z(node) = sum over the (up to four) agglomerates around the node of
@@ -694,6 +726,7 @@ __global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nel
   const int s = blockIdx.y;
   const int N = 2 * H + 1, NP = N, nbP = 2 * NP;
   const int R = PC_GROUP * nsys;
+  const double invH2 = 1.0 / ((double)H * H);
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn1;
        node += (long long)gridDim.x * blockDim.x) {
     const int x = node % (nelx + 1), y = node / (nelx + 1);
@@ -708,7 +741,7 @@ __global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nel
         const long long l = (long long)(y - (J - 1) * H) * N + (x - (I - 1) * H);
         if (part != 2 && abs(x - I * H) < H && abs(y - J * H) < H) {
           const int t = type_of[i], k = kept[t];
-          const double chi = hat(x, I * H, H) * hat(y, J * H, H);
+          const double chi = (double)((H - abs(x - I * H)) * (H - abs(y - J * H))) * invH2;
           const T* pp = psi + ((long long)t * N * N + l) * 2 * kmax;
           const double* u = uc + (long long)s * Nt + coff[i];
           double ax = 0.0, ay = 0.0;
@@ -720,10 +753,11 @@ __global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nel
           zy = fma(chi, ay, zy);
         }
         if (part != 1) {
-          const long long base = (long long)agg_group[i] * NP * nbP + 2 * l;
+          const int lb = y - (J - 1) * H, la = x - (I - 1) * H;
           const int col = agg_slot[i] * nsys + s;
-          zx += (double)Xg[base * R + col];
-          zy += (double)Xg[(base + 1) * R + col];
+          const long long base = (((long long)agg_group[i] * NP + lb) * R + col) * nbP + 2 * la;
+          zx += (double)Xg[base];
+          zy += (double)Xg[base + 1];
         }
       }
     const uint8_t f = nmask[node];
@@ -810,7 +844,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   // 2. agglomerate matrices, shifted factor, eigen-solve
   const int NA = pc.NA, nbA = pc.nbA;
   const long long nnA = (long long)nbA * nbA, nA = (long long)NA * nbA;
-  const int q = std::min(2 * pc.kmax + 4, 2 * MSTOPO_MAX_EIG);
+  // subspace dimension: 2k + 4 rounded up to a multiple of 4 (compile-time variants)
+  const int q = std::min(((2 * pc.kmax + 4) + 3) / 4 * 4, 2 * MSTOPO_MAX_EIG);
   double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY;
   uint8_t* dfree_;
   int* d_st;
@@ -842,9 +877,15 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   ea.K0 = K0;
   ea.err = h->d_flag + 1;
   size_t esm = (size_t)(nnA + 2 * nbA * q + 6 * q * q + 2 * q) * 8;
-  CKB(cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  if (esm > 227 * 1024) {
+    h->err = "n_eig too large for this H: the eigen-solve workspace exceeds shared memory";
+    return MSTOPO_INVALID_ARG;
+  }
   CKB(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), s));
-  note_launch(), k_eigen<<<T, PC_THREADS, esm, s>>>(ea);
+  {
+    cudaError_t le = launch_eigen(q, T, esm, s, ea);
+    CKB(le);
+  }
   CKB(cudaGetLastError());
   std::vector<int> fst(T);
   CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1019,6 +1060,19 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   return MSTOPO_OK;
 }
 
+template <typename T, int R>
+static cudaError_t launch_patch(mstopo_handle* h, const T* r, int nsys, size_t sm, const T* Linv,
+                                const T* C, T* Xg) {
+  Precond& pc = h->pc;
+  cudaError_t e = cudaFuncSetAttribute(k_patch_solve<T, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_patch_solve<T, R><<<pc.n_groups, SOLVE_THREADS, sm, h->s>>>(
+      r, h->n_dof, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_first,
+      pc.d_grp_count, pc.d_perm, pc.d_pfree, Linv, C, Xg, h->d_flag + 1);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int part,
                               const T* psi, const T* Linv, const T* C, T* Xg) {
@@ -1034,18 +1088,19 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int 
     prof_end(h->prof, PROF_COARSE, pa, s);
   }
   if (part != 1) {
-    const int NP = pc.NP, nbP = pc.nbP, R = PC_GROUP * nsys;
+    const int nbP = pc.nbP, R = PC_GROUP * nsys;
     const int nbuf = sizeof(T) == 4 ? 2 : 1;
     size_t sm = ((size_t)nbuf * nbP * nbP + 2 * (size_t)nbP * R) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_patch_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     cudaEvent_t pa = prof_begin(h->prof, s);
-    note_launch(), k_patch_solve<T><<<pc.n_groups, PC_THREADS, sm, s>>>(r, n, nsys, h->nelx, h->nely, pc.H, pc.ncx,
-                                                          pc.d_grp_type, pc.d_grp_first,
-                                                          pc.d_grp_count, pc.d_perm, pc.d_pfree, Linv, C, Xg,
-                                                          h->d_flag + 1);
+    cudaError_t e;
+    switch (R) {
+      case 4: e = launch_patch<T, 4>(h, r, nsys, sm, Linv, C, Xg); break;
+      case 8: e = launch_patch<T, 8>(h, r, nsys, sm, Linv, C, Xg); break;
+      case 12: e = launch_patch<T, 12>(h, r, nsys, sm, Linv, C, Xg); break;
+      default: e = launch_patch<T, 16>(h, r, nsys, sm, Linv, C, Xg); break;
+    }
+    if (e != cudaSuccess) return e;
     prof_end(h->prof, PROF_PATCH, pa, s);
-    (void)NP;
   }
   note_launch(), k_combine<T><<<dim3(608, nsys), 256, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
