@@ -169,6 +169,27 @@ mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t 
 mstopo_status mstopo_get_eigenpairs(mstopo_handle* h, int32_t I, int32_t J, double* lambda,
                                     double* psi, int32_t* n_kept);
 
+/* ---- an entry point that allocates nothing (no counterpart in the paper) ------------- */
+
+/* y = K(E) u on the free DOFs with the FP32 matrix-free matvec, exactly the arithmetic of
+ * mstopo_apply_K(h, k, MSTOPO_MIXED, u, y), but without a handle and without allocating
+ * any device memory.  For callers that cannot call cudaMalloc: code whose device memory is
+ * owned by another allocator or a fixed arena, or that must not trigger the device-wide
+ * synchronisation cudaMalloc can cause.
+ *   u, y:  DEVICE, nodal layout, double;  E: DEVICE, element layout, float (Young's moduli);
+ *   fixed: DEVICE, nodal layout of uint8 (nonzero = Dirichlet DOF);  nu: Poisson's ratio;
+ *   stream: cudaStream_t or NULL.  The call returns after the stream has been synchronised.
+ * Work space: one static device array of about 36 MB that every GPU loading this library
+ * holds until the process exits; at most 4,194,304 DOFs (2 (nelx+1)(nely+1) <= 2^22),
+ * larger meshes return MSTOPO_INVALID_ARG before any GPU work.  The first call on a device
+ * looks the array's address up on that device (make that first call before any stream
+ * capture).  All calls share the array: calls that overlap on the GPU race.
+ * Errors: INVALID_ARG (null pointer, non-positive size, nu outside [0, 0.5), too many DOFs),
+ * CUDA_ERROR. */
+mstopo_status mstopo_apply_K_f32_noalloc(const double* u, double* y, const float* E,
+                                        const uint8_t* fixed, int32_t nelx, int32_t nely,
+                                        double nu, void* stream);
+
 /* ---- measurement (not part of the paper's method) ----------------------------------- */
 
 typedef struct {

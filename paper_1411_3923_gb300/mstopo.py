@@ -63,7 +63,7 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_build_preconditioner", "mstopo_solve", "mstopo_solve_host",
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
            "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
-           "mstopo_get_stats"]
+           "mstopo_get_stats", "mstopo_apply_K_f32_noalloc"]
 
 
 def load(path: str = LIB_PATH):
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "mstopo_get_eigenpairs": ([vp, i32, i32, vp, vp, vp], i32),
         "mstopo_set_profiling": ([vp, i32], i32),
         "mstopo_get_stats": ([vp, C.POINTER(_Stats)], i32),
+        "mstopo_apply_K_f32_noalloc": ([vp, vp, vp, vp, i32, i32, dbl, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
