@@ -194,8 +194,7 @@ def run_ours(args, rank: int, world: int):
         step(fp64, new_events())
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps of the MIXED path ----
-    mixed.set_profiling(True)
+    # ---- timed region: K steps of the MIXED path (no per-kernel events: CUDA graphs on) ----
     launches0 = mixed.stats()["launches"]
     dev_id = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(
         torch.cuda.get_device_properties(dev), "uuid") else str(dev.index)
@@ -223,9 +222,17 @@ def run_ours(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
+    launches = mixed.stats()["launches"] - launches0
+    # ---- profiled pass: the same step with per-kernel events (graphs off) ----
+    mixed.set_profiling(True)
+    for _ in range(max(1, min(2, args.steps))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step(mixed, new_events())
+    torch.cuda.synchronize()
     st = mixed.stats()
-    launches = st["launches"] - launches0
     mixed.set_profiling(False)
+    nprof = max(1, min(2, args.steps))
 
     solve_ms = statistics.mean(p["solve"] for p in per)
     step_ms = statistics.mean(p["step"] for p in per)
@@ -243,7 +250,7 @@ def run_ours(args, rank: int, world: int):
 
     # ---- roofline of the dominant profiled kernel in the mixed step ----
     kern = {k: v for k, v in st.items() if isinstance(v, dict)}
-    nsteps = args.steps
+    nsteps = nprof
     wl_N = 2 * wl.H + 1
     nb = 2 * wl_N
     n_agg = (wl.nelx // wl.H + 1) * (wl.nely // wl.H + 1)

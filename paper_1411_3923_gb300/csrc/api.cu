@@ -2,6 +2,7 @@
 // Host orchestration only: argument checks, workspace ownership, kernel sequencing on the
 // handle's stream.  Every step of the numerical path runs in the kernels of this library.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -90,6 +91,16 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     return fail(MSTOPO_INVALID_ARG);
   }
   h->s = (cudaStream_t)d->stream;
+  if (!h->s) {
+    // a blocking stream of our own (it orders with the legacy default stream) so that the
+    // flexible-CG chunks can be captured into CUDA graphs
+    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) {
+      h->err = "could not create a stream";
+      return fail(MSTOPO_CUDA_ERROR);
+    }
+    h->s = h->own_stream;
+  }
+  if (getenv("MSTOPO_NO_GRAPHS")) h->graphs_enabled = 0;
   h->nelx = d->nelx;
   h->nely = d->nely;
   h->n_nodes = (long long)(d->nelx + 1) * (d->nely + 1);
@@ -131,11 +142,13 @@ void mstopo_destroy(mstopo_handle* h) {
   precond_free(h->pc);
   solver_free(h->sv);
   prof_free(h->prof);
+  if (h->fcg_graph.exec) cudaGraphExecDestroy(h->fcg_graph.exec);
   void* ptrs[] = {h->d_K0, h->d_nmask, h->d_rho, h->d_rho_tilde, h->d_wsum, h->d_rbar, h->d_drbar,
                   h->d_E64, h->d_E32, h->d_gfine, h->d_gdesign, h->d_w, h->d_flag, h->d_u_all,
                   h->d_f_all, h->d_host_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
 
@@ -227,6 +240,7 @@ mstopo_status mstopo_build_preconditioner(mstopo_handle* h, int32_t ref, mstopo_
   }
   CHECK_ARG(ref < h->n_eta, "reference realisation out of range");
   h->pc_ref = ref;
+  h->pc_generation++;
   mstopo_status st = precond_build(h, ref, info);
   if (st != MSTOPO_OK) h->pc.built = 0;
   return st;

@@ -101,7 +101,14 @@ struct FcgScalars {            // per system, on the device
   int active;                  // 1 while iterating
   int status;                  // mstopo_status
   int iters;
-  int pad;
+  int restart;                 // 1: the next direction is p = z (first step)
+};
+
+struct FcgGraph {              // one captured chunk of flexible-CG iterations
+  cudaGraphExec_t exec = nullptr;
+  int sys0 = -1, nsys = 0;
+  long long generation = -1;
+  long long launches = 0;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -125,6 +132,10 @@ struct Precond {
   uint8_t* d_pfree = nullptr;       // [T][NP*nbP] free DOFs of the patch box
   double* d_pLinv64 = nullptr; double* d_pC64 = nullptr;
   float* d_pLinv32 = nullptr;  float* d_pC32 = nullptr;
+  // packed stage blocks for the cluster patch solve: [T][NL][4 ranks][2][rpc][nbs]
+  double* d_pf64 = nullptr; double* d_pb64 = nullptr;
+  float* d_pf32 = nullptr;  float* d_pb32 = nullptr;
+  int rpc = 0, nbs = 0, patches_per_group = 1;
   // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
   double* d_lambda = nullptr; double* d_psi64 = nullptr; float* d_psi32 = nullptr;
   double* d_eigres = nullptr;       // [T] residual norms
@@ -182,6 +193,10 @@ struct mstopo_handle {
   double* d_f_all = nullptr;        // load used for it
   double* d_host_stage = nullptr;   // device staging for the host-pointer entry point
   Prof prof;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
+  int graphs_enabled = 1;
+  long long pc_generation = 0;        // bumped by every preconditioner build
+  FcgGraph fcg_graph;
 };
 
 // precond.cu

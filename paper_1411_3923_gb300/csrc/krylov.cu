@@ -24,6 +24,7 @@
 
 #define RB MSTOPO_RED_BLOCKS
 #define RT 256
+#define FCG_CHUNK 8   // iterations between host checks (one CUDA graph)
 
 // --------------------------------------------------------------------------- reductions
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -124,11 +125,12 @@ cudaError_t launch_mask_copy(const double* a, double* b, const uint8_t* nmask, l
 
 // --------------------------------------------------------------------------- FCG steps
 // beta = -(z^T q_prev) / (p_prev^T q_prev); zero on the first step after a (re)start
-__global__ void k_scalar_beta(FcgScalars* sc, const double* __restrict__ zq, int restart) {
+__global__ void k_scalar_beta(FcgScalars* sc, const double* __restrict__ zq) {
   FcgScalars& c = sc[threadIdx.x];
   if (!c.active) return;
   c.zq = zq[threadIdx.x];
-  c.beta = restart ? 0.0 : -c.zq / c.pq_prev;
+  c.beta = c.restart ? 0.0 : -c.zq / c.pq_prev;
+  c.restart = 0;
 }
 
 // p = z + beta p  (PT = float in MIXED mode, double in FP64 mode)
@@ -363,6 +365,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   memset(&init, 0, sizeof(init));
   init.active = 1;
   init.status = MSTOPO_OK;
+  init.restart = 1;
   for (int s = 0; s < nsys; ++s) sv.h_sc[s] = init;
   CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
   double* vtmp = sv.partials + (size_t)MSTOPO_MAX_SYS * 3 * RB;   // small scratch [nsys]
@@ -377,7 +380,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
   double rr_last[MSTOPO_MAX_SYS];
-  int done[MSTOPO_MAX_SYS] = {0}, repl[MSTOPO_MAX_SYS] = {0}, restart = 1;
+  int done[MSTOPO_MAX_SYS] = {0}, repl[MSTOPO_MAX_SYS] = {0};
   for (int s = 0; s < nsys; ++s) {
     rr_last[s] = sv.h_sc[s].rr;
     if (sv.h_sc[s].ff == 0.0) {
@@ -388,53 +391,85 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   }
   const float* E32 = h->d_E32 + (long long)sys0 * h->n_el;
   const double* E64 = h->d_E64 + (long long)sys0 * h->n_el;
-  const int chunk = 4;
+  // one flexible-CG iteration for all systems (kernels skip finished systems)
+  auto iteration = [&]() -> mstopo_status {
+    mstopo_status s2 = precond(h, nsys);
+    if (s2 != MSTOPO_OK) return s2;
+    if (mixed) CK(launch_dot_partials_f32(sv.z32, sv.q32, n, nsys, n, sv.partials, h->s));
+    else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));
+    CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+    note_launch(), k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp);
+    CK(cudaGetLastError());
+    if (mixed) {
+      note_launch(), k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
+      CK(cudaGetLastError());
+      cudaEvent_t pa = prof_begin(h->prof, h->s);
+      CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
+                           h->n_el, h->s));
+      prof_end(h->prof, PROF_MATVEC32, pa, h->s);
+      note_launch(), k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
+    } else {
+      note_launch(), k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
+      CK(cudaGetLastError());
+      cudaEvent_t pa = prof_begin(h->prof, h->s);
+      CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
+                           h->n_el, h->s));
+      prof_end(h->prof, PROF_MATVEC64, pa, h->s);
+      note_launch(), k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
+    }
+    CK(cudaGetLastError());
+    note_launch(), k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
+    CK(cudaGetLastError());
+    if (mixed)
+      note_launch(), k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
+                                                          sv.partials, sv.sc);
+    else
+      note_launch(), k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
+                                                           n, sv.partials, sv.sc);
+    CK(cudaGetLastError());
+    note_launch(), k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
+    CK(cudaGetLastError());
+    return MSTOPO_OK;
+  };
+  const int chunk = FCG_CHUNK;
   int total_iters = 0;
+  bool first_chunk = true;
   while (true) {
     int n_active = 0;
     for (int s = 0; s < nsys; ++s) n_active += !done[s];
     if (n_active == 0) break;
-    for (int it = 0; it < chunk; ++it) {
-      st = precond(h, nsys);
-      if (st != MSTOPO_OK) return st;
-      if (!restart) {
-        if (mixed) CK(launch_dot_partials_f32(sv.z32, sv.q32, n, nsys, n, sv.partials, h->s));
-        else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));
-        CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+    // the first chunk runs directly (it also sets kernel attributes); later chunks replay
+    // one captured graph of `chunk` iterations, unless per-kernel profiling is on
+    const bool use_graph = !first_chunk && !h->prof.on && h->graphs_enabled;
+    if (use_graph) {
+      FcgGraph& gr = h->fcg_graph;
+      if (!gr.exec || gr.sys0 != sys0 || gr.nsys != nsys || gr.generation != h->pc_generation) {
+        if (gr.exec) { cudaGraphExecDestroy(gr.exec); gr.exec = nullptr; }
+        cudaGraph_t graph;
+        const long long l0 = g_launch_count.load();
+        CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        mstopo_status cs = MSTOPO_OK;
+        for (int it = 0; it < chunk && cs == MSTOPO_OK; ++it) cs = iteration();
+        cudaError_t ce = cudaStreamEndCapture(h->s, &graph);
+        if (cs != MSTOPO_OK) return cs;
+        CK(ce);
+        CK(cudaGraphInstantiate(&gr.exec, graph, 0));
+        cudaGraphDestroy(graph);
+        gr.launches = g_launch_count.load() - l0;
+        g_launch_count.fetch_sub(gr.launches);   // counted per replay below
+        gr.sys0 = sys0;
+        gr.nsys = nsys;
+        gr.generation = h->pc_generation;
       }
-      note_launch(), k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, restart);
-      CK(cudaGetLastError());
-      restart = 0;
-      if (mixed) {
-        note_launch(), k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
-        CK(cudaGetLastError());
-        cudaEvent_t pa = prof_begin(h->prof, h->s);
-        CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
-                             h->n_el, h->s));
-        prof_end(h->prof, PROF_MATVEC32, pa, h->s);
-        note_launch(), k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
-      } else {
-        note_launch(), k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
-        CK(cudaGetLastError());
-        cudaEvent_t pa = prof_begin(h->prof, h->s);
-        CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
-                             h->n_el, h->s));
-        prof_end(h->prof, PROF_MATVEC64, pa, h->s);
-        note_launch(), k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
+      CK(cudaGraphLaunch(gr.exec, h->s));
+      g_launch_count.fetch_add(gr.launches);
+    } else {
+      for (int it = 0; it < chunk; ++it) {
+        st = iteration();
+        if (st != MSTOPO_OK) return st;
       }
-      CK(cudaGetLastError());
-      note_launch(), k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
-      CK(cudaGetLastError());
-      if (mixed)
-        note_launch(), k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
-                                                            sv.partials, sv.sc);
-      else
-        note_launch(), k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
-                                                             n, sv.partials, sv.sc);
-      CK(cudaGetLastError());
-      note_launch(), k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
-      CK(cudaGetLastError());
     }
+    first_chunk = false;
     total_iters += chunk;
     int werr = 0;
     CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));

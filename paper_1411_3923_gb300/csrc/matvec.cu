@@ -8,8 +8,8 @@
 //
 // Work split: one thread per node column i, a strip of MV_TY node rows per thread; the 3x3
 // neighbourhood and the 2x2 surrounding moduli slide up the strip in registers, so each
-// node row of u and each element row of E is loaded once per thread (neighbour columns are
-// L1 hits).  Grid: ceil((nelx+1)/MV_TX) x ceil((nely+1)/MV_TY) x systems.
+// node row of u and each element row of E is loaded once (the neighbour columns come from
+// the adjacent lanes).  Grid: ceil((nelx+1)/MV_TX) x ceil((nely+1)/MV_TY) x systems.
 #include "internal.cuh"
 
 #define MV_TX 128
@@ -89,6 +89,24 @@ __device__ __forceinline__ void blk(T& ax, T& ay, const T* b, T dx, T dy) {
 }
 
 template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type shfl_up2(typename Vec2<T>::type v) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type shfl_down2(typename Vec2<T>::type v) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+
+// Rows are processed in chunks of MV_U: the loads of the next MV_U node rows and element rows
+// are all issued before any of them is used, so each thread keeps MV_U rows of loads in
+// flight.  A warp covers 32 consecutive node columns; the left/right neighbours come from
+// the adjacent lanes by shuffles (edge lanes load their own).
+#define MV_U 4
+template <typename T>
 __global__ void __launch_bounds__(MV_TX) k_matvec(const T* __restrict__ u, T* __restrict__ y,
                                                   const T* __restrict__ E,
                                                   const uint8_t* __restrict__ nmask, int nelx,
@@ -96,78 +114,107 @@ __global__ void __launch_bounds__(MV_TX) k_matvec(const T* __restrict__ u, T* __
                                                   long long vec_stride, long long e_stride) {
   typedef typename Vec2<T>::type V;
   const int nx1 = nelx + 1, ny1 = nely + 1;
+  const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * MV_TX + threadIdx.x;
   const int j0 = blockIdx.y * MV_TY;
-  if (i >= nx1) return;
+  const bool in = i < nx1;
   u += blockIdx.z * vec_stride;
   y += blockIdx.z * vec_stride;
   E += blockIdx.z * e_stride;
-  // window rows: 0 -> j-1, 1 -> j, 2 -> j+1 ; columns 0 -> i-1, 1 -> i, 2 -> i+1
-  V w[3][3];
-  T el[2][2];   // [row: j-1, j][col: i-1, i]
+  // window rows: 0 -> j-1, 1 -> j, 2 -> j+1 ; columns: left (i-1), centre (i), right (i+1)
+  V wl[3], wc[3], wr[3];
+  T el[2], ec[2];   // moduli of elements (i-1, row) and (i, row) for rows j-1 (0) and j (1)
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) w[r][q] = load_node(u, nmask, i - 1 + q, j0 - 1 + r, nx1, ny1);
-  el[1][0] = load_E(E, i - 1, j0 - 1, nelx, nely);
-  el[1][1] = load_E(E, i, j0 - 1, nelx, nely);
+  for (int r = 0; r < 2; ++r) {
+    const int jj = j0 - 1 + r;
+    V cv = load_node(u, nmask, i, jj, nx1, ny1);
+    V lv = shfl_up2<T>(cv), rv = shfl_down2<T>(cv);
+    if (lane == 0) lv = load_node(u, nmask, i - 1, jj, nx1, ny1);
+    if (lane == 31) rv = load_node(u, nmask, i + 1, jj, nx1, ny1);
+    wl[r] = lv; wc[r] = cv; wr[r] = rv;
+  }
+  {
+    T ce = load_E(E, i, j0 - 1, nelx, nely);
+    T le = __shfl_up_sync(0xffffffffu, ce, 1);
+    if (lane == 0) le = load_E(E, i - 1, j0 - 1, nelx, nely);
+    el[1] = le; ec[1] = ce;
+  }
   const int jend = min(j0 + MV_TY, ny1);
-  for (int j = j0; j < jend; ++j) {
+  for (int jb = j0; jb < jend; jb += MV_U) {
+    V pc[MV_U], pe2[MV_U];
+    T pe[MV_U], ple[MV_U];
+    uint8_t pm[MV_U];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) w[2][q] = load_node(u, nmask, i - 1 + q, j + 1, nx1, ny1);
-    el[0][0] = el[1][0];
-    el[0][1] = el[1][1];
-    el[1][0] = load_E(E, i - 1, j, nelx, nely);
-    el[1][1] = load_E(E, i, j, nelx, nely);
-    const T cx = w[1][1].x, cy = w[1][1].y;
-    // neighbour differences d[r][q] = u(i-1+q, j-1+r) - u(i, j)
-    T dxv[3][3], dyv[3][3];
+    for (int r = 0; r < MV_U; ++r) {
+      const int jn = jb + 1 + r;
+      pc[r] = load_node(u, nmask, i, jn, nx1, ny1);
+      pe2[r] = load_node(u, nmask, lane == 0 ? i - 1 : i + 1, jn, nx1, ny1);
+      pe[r] = load_E(E, i, jb + r, nelx, nely);
+      ple[r] = load_E(E, i - 1, jb + r, nelx, nely);
+      pm[r] = (in && jb + r < ny1) ? nmask[(long long)(jb + r) * nx1 + i] : (uint8_t)3;
+    }
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        dxv[r][q] = w[r][q].x - cx;
-        dyv[r][q] = w[r][q].y - cy;
+    for (int r = 0; r < MV_U; ++r) {
+      const int j = jb + r;
+      {
+        V cv = pc[r];
+        V lv = shfl_up2<T>(cv), rv = shfl_down2<T>(cv);
+        if (lane == 0) lv = pe2[r];
+        if (lane == 31) rv = pe2[r];
+        wl[2] = lv; wc[2] = cv; wr[2] = rv;
+        T ce = pe[r];
+        T le = __shfl_up_sync(0xffffffffu, ce, 1);
+        if (lane == 0) le = ple[r];
+        el[0] = el[1]; ec[0] = ec[1];
+        el[1] = le; ec[1] = ce;
       }
-    T yx = T(0), yy = T(0);
-    {  // LL element (i-1, j-1): others (i-1,j-1), (i,j-1), (i-1,j)
-      T ax = T(0), ay = T(0);
-      blk(ax, ay, c.c[0][0], dxv[0][0], dyv[0][0]);
-      blk(ax, ay, c.c[0][1], dxv[0][1], dyv[0][1]);
-      blk(ax, ay, c.c[0][2], dxv[1][0], dyv[1][0]);
-      yx = fma(el[0][0], ax, yx); yy = fma(el[0][0], ay, yy);
-    }
-    {  // LR element (i, j-1): others (i,j-1), (i+1,j-1), (i+1,j)
-      T ax = T(0), ay = T(0);
-      blk(ax, ay, c.c[1][0], dxv[0][1], dyv[0][1]);
-      blk(ax, ay, c.c[1][1], dxv[0][2], dyv[0][2]);
-      blk(ax, ay, c.c[1][2], dxv[1][2], dyv[1][2]);
-      yx = fma(el[0][1], ax, yx); yy = fma(el[0][1], ay, yy);
-    }
-    {  // UL element (i-1, j): others (i-1,j), (i,j+1), (i-1,j+1)
-      T ax = T(0), ay = T(0);
-      blk(ax, ay, c.c[2][0], dxv[1][0], dyv[1][0]);
-      blk(ax, ay, c.c[2][1], dxv[2][1], dyv[2][1]);
-      blk(ax, ay, c.c[2][2], dxv[2][0], dyv[2][0]);
-      yx = fma(el[1][0], ax, yx); yy = fma(el[1][0], ay, yy);
-    }
-    {  // UR element (i, j): others (i+1,j), (i+1,j+1), (i,j+1)
-      T ax = T(0), ay = T(0);
-      blk(ax, ay, c.c[3][0], dxv[1][2], dyv[1][2]);
-      blk(ax, ay, c.c[3][1], dxv[2][2], dyv[2][2]);
-      blk(ax, ay, c.c[3][2], dxv[2][1], dyv[2][1]);
-      yx = fma(el[1][1], ax, yx); yy = fma(el[1][1], ay, yy);
-    }
-    const long long n = (long long)j * nx1 + i;
-    const uint8_t f = nmask[n];
-    V out;
-    out.x = (f & 1) ? T(0) : yx;
-    out.y = (f & 2) ? T(0) : yy;
-    reinterpret_cast<V*>(y)[n] = out;
+      const T cx = wc[1].x, cy = wc[1].y;
+      // neighbour differences u(i-1+q, j-1+r) - u(i, j)
+      T dxv[3][3], dyv[3][3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      w[0][q] = w[1][q];
-      w[1][q] = w[2][q];
+      for (int rr = 0; rr < 3; ++rr) {
+        dxv[rr][0] = wl[rr].x - cx; dyv[rr][0] = wl[rr].y - cy;
+        dxv[rr][1] = wc[rr].x - cx; dyv[rr][1] = wc[rr].y - cy;
+        dxv[rr][2] = wr[rr].x - cx; dyv[rr][2] = wr[rr].y - cy;
+      }
+      T yx = T(0), yy = T(0);
+      {  // LL element (i-1, j-1): others (i-1,j-1), (i,j-1), (i-1,j)
+        T ax = T(0), ay = T(0);
+        blk(ax, ay, c.c[0][0], dxv[0][0], dyv[0][0]);
+        blk(ax, ay, c.c[0][1], dxv[0][1], dyv[0][1]);
+        blk(ax, ay, c.c[0][2], dxv[1][0], dyv[1][0]);
+        yx = fma(el[0], ax, yx); yy = fma(el[0], ay, yy);
+      }
+      {  // LR element (i, j-1): others (i,j-1), (i+1,j-1), (i+1,j)
+        T ax = T(0), ay = T(0);
+        blk(ax, ay, c.c[1][0], dxv[0][1], dyv[0][1]);
+        blk(ax, ay, c.c[1][1], dxv[0][2], dyv[0][2]);
+        blk(ax, ay, c.c[1][2], dxv[1][2], dyv[1][2]);
+        yx = fma(ec[0], ax, yx); yy = fma(ec[0], ay, yy);
+      }
+      {  // UL element (i-1, j): others (i-1,j), (i,j+1), (i-1,j+1)
+        T ax = T(0), ay = T(0);
+        blk(ax, ay, c.c[2][0], dxv[1][0], dyv[1][0]);
+        blk(ax, ay, c.c[2][1], dxv[2][1], dyv[2][1]);
+        blk(ax, ay, c.c[2][2], dxv[2][0], dyv[2][0]);
+        yx = fma(el[1], ax, yx); yy = fma(el[1], ay, yy);
+      }
+      {  // UR element (i, j): others (i+1,j), (i+1,j+1), (i,j+1)
+        T ax = T(0), ay = T(0);
+        blk(ax, ay, c.c[3][0], dxv[1][2], dyv[1][2]);
+        blk(ax, ay, c.c[3][1], dxv[2][2], dyv[2][2]);
+        blk(ax, ay, c.c[3][2], dxv[2][1], dyv[2][1]);
+        yx = fma(ec[1], ax, yx); yy = fma(ec[1], ay, yy);
+      }
+      if (in && j < jend) {
+        const uint8_t f = pm[r];
+        V out;
+        out.x = (f & 1) ? T(0) : yx;
+        out.y = (f & 2) ? T(0) : yy;
+        reinterpret_cast<V*>(y)[(long long)j * nx1 + i] = out;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) { wl[rr] = wl[rr + 1]; wc[rr] = wc[rr + 1]; wr[rr] = wr[rr + 1]; }
     }
   }
 }

@@ -33,7 +33,11 @@
 
 #define PC_THREADS 256
 #define SOLVE_THREADS 320   // 160 rows x 2 threads per pass covers nb = 2(2H+1) up to H = 39
-#define PC_GROUP 4          // patches of one type solved together per CTA (x systems)
+#define PATCH_HALVES 2      // row halves of every line in the patch solve
+#define PATCH_S 8           // threads sharing one row pair in the patch solve
+#define PATCH_THREADS 288   // >= ceil(hrows / 2) * PATCH_S = 33 * 8 for H = 32 (warp multiple)
+#define PATCH_COLS 16       // right-hand-side columns per CTA (patches x systems), at most
+#define PATCH_GROUP 4       // patches per CTA
 #define EIG_MAX_SWEEPS 80
 #define EIG_TOL 1e-7
 #define EIG_SHIFT 1e-5
@@ -667,102 +671,314 @@ __global__ void k_coarse_gemv(const double* __restrict__ Kinv, const double* __r
   }
 }
 
-// Patch solves: one CTA per group of up to PC_GROUP agglomerates of one type, all systems.
-// Right-hand side columns: slot = g * nsys + s (R = PC_GROUP * nsys of them).
-// Work buffer Xg [group][line][R][nbP] (DOFs fastest).
+// Patch solves, one CTA per group of up to P patches of one type (all systems: R = 4Q
+// right-hand-side columns, zero padded).  The block-tridiagonal factor is applied as
+//   forward   y_k = Linv_k b_k - W_k y_{k-1}        (W_k = Linv_k C_{k-1})
+//   backward  x_k = Linv_k^T y_k - V_k x_{k+1}     (V_k = Linv_k^T C_k^T)
+// so each line is one fused product of two known vectors.  The rows of every line are
+// processed in two halves; each half-stage block [A rows | B rows] (A = Linv_k or Linv_k^T,
+// B = W_k or V_k, hrows rows of stride nbs) is one bulk copy, double-buffered (FP32) so the
+// next half loads while the current one is used.  S threads share a row (float4 reads of
+// the row and of the vectors, shuffle reduction).  The right-hand sides are read straight
+// from r at each forward line; y_k is kept in the work buffer for the backward sweep, which
+// overwrites line k with x_k.  Work buffer Xg: [group][line][nb][R] (y), then [group][line][R][nb] (x).
+// R consecutive values (R a multiple of 4, 16-byte aligned) from shared memory
 template <typename T, int R>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_patch_solve(
+__device__ __forceinline__ void load_vec(const T* p, T* v) {
+  if (sizeof(T) == 4) {
+#pragma unroll
+    for (int j = 0; j < R; j += 4) {
+      const float4 w = *reinterpret_cast<const float4*>(p + j);
+      v[j] = w.x; v[j + 1] = w.y; v[j + 2] = w.z; v[j + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; j += 2) {
+      const double2 w = *reinterpret_cast<const double2*>(p + j);
+      v[j] = w.x; v[j + 1] = w.y;
+    }
+  }
+}
+
+template <typename T, int Q, int NBUF>
+__global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
     const T* __restrict__ r, long long stride, int nsys, int nelx, int nely, int H, int ncx,
     const int* __restrict__ grp_type, const int* __restrict__ grp_first,
     const int* __restrict__ grp_count, const int* __restrict__ perm,
-    const uint8_t* __restrict__ pfree, const T* __restrict__ Linv, const T* __restrict__ C,
-    T* __restrict__ Xg, int* __restrict__ err) {
+    const uint8_t* __restrict__ pfree, const T* __restrict__ fwd, const T* __restrict__ bwd,
+    int nbs, int hrows, T* __restrict__ Xg, int* __restrict__ err) {
+  constexpr int R = 4 * Q;
+  constexpr int S = PATCH_S;
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_abort;
+  __shared__ int s_node[PATCH_COLS];   // patch origin per column block: (I-1)H, (J-1)H packed
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* smem = reinterpret_cast<T*>(smraw);
   const int g = blockIdx.x;
   const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
-  const int N = 2 * H + 1, nb = 2 * N;
+  const int N = 2 * H + 1, nb = 2 * N, NL = N;
+  const long long blk = 2LL * hrows * nbs;
+  const uint32_t bytes = (uint32_t)(blk * sizeof(T));
+  T* stg = reinterpret_cast<T*>(smraw);                 // [NBUF][2][hrows][nbs]
+  T* vb = stg + NBUF * blk;                             // [nbs][R] input b_k or y_k
+  T* prev = vb + (long long)nbs * R;                    // [nbs][R] y_{k-1} or x_{k+1}
+  T* cur = prev + (long long)nbs * R;                   // [nbs][R] this line's result
   const uint8_t* fr = pfree + (long long)type * N * nb;
-  const long long nn = (long long)nb * nb;
-  T* X = Xg + (long long)g * N * nb * R;
-  // gather: X[line][p*nsys+s][2a+c] = r_s(node) on the free DOFs of the patch box
-  for (long long t = threadIdx.x; t < (long long)N * nb * R; t += blockDim.x) {
-    const int rr = t % nb;
-    const int col = (t / nb) % R;
-    const int line = t / ((long long)nb * R);
-    const int p = col / nsys, s = col % nsys;
-    T v = T(0);
-    if (p < cnt && fr[(long long)line * nb + rr]) {
+  T* X = Xg + (long long)g * NL * R * nb;
+  if (threadIdx.x < PATCH_COLS) {
+    const int p = threadIdx.x;
+    int v = -1;
+    if (p < cnt) {
       const int ia = perm[first + p];
-      const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-      const int x = (I - 1) * H + (rr >> 1), y = (J - 1) * H + line;
-      if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
-        v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (rr & 1)];
+      v = ia;
     }
-    X[t] = v;
+    s_node[p] = v;
+  }
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
   }
   __syncthreads();
-  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
-  T* stage = smem;
-  T* t0 = stage + NBUF * nn;
-  T* t1 = t0 + nb * R;
-  bt_solve_bulk<T, NBUF, R, true>(Linv + (long long)type * N * nn,
-                                  C + (long long)type * (N - 1) * nn, nb, N, X, stage, t0, t1,
-                                  bars, err);
-}
-
-// z(node) = sum over the (up to four) agglomerates around the node of
-//           chi_i psi_i uc_i  (coarse part)  +  patch solution of omega_i at the node
-template <typename T>
-__global__ void k_combine(T* __restrict__ z, long long stride, int nsys, int nelx, int nely,
-                          int H, int ncx, int ncy, const int* __restrict__ type_of,
-                          const int* __restrict__ kept, const int* __restrict__ coff,
-                          const T* __restrict__ psi, int kmax, const double* __restrict__ uc,
-                          int Nt, const int* __restrict__ agg_group,
-                          const int* __restrict__ agg_slot, const T* __restrict__ Xg,
-                          const uint8_t* __restrict__ nmask, int part) {
-  const long long nn1 = (long long)(nelx + 1) * (nely + 1);
-  const int s = blockIdx.y;
-  const int N = 2 * H + 1, NP = N, nbP = 2 * NP;
-  const int R = PC_GROUP * nsys;
-  const double invH2 = 1.0 / ((double)H * H);
-  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn1;
-       node += (long long)gridDim.x * blockDim.x) {
-    const int x = node % (nelx + 1), y = node / (nelx + 1);
-    double zx = 0.0, zy = 0.0;
-    const int Ib = x / H, Jb = y / H;
-    // agglomerates whose closed box contains the node: |x - IH| <= H, |y - JH| <= H.  chi
-    // vanishes on the box edge, and the patch solution vanishes on artificial edge nodes.
-    for (int J = max(Jb - 1, 0); J <= min(Jb + 1, ncy); ++J)
-      for (int I = max(Ib - 1, 0); I <= min(Ib + 1, ncx); ++I) {
-        if (abs(x - I * H) > H || abs(y - J * H) > H) continue;
-        const int i = J * (ncx + 1) + I;
-        const long long l = (long long)(y - (J - 1) * H) * N + (x - (I - 1) * H);
-        if (part != 2 && abs(x - I * H) < H && abs(y - J * H) < H) {
-          const int t = type_of[i], k = kept[t];
-          const double chi = (double)((H - abs(x - I * H)) * (H - abs(y - J * H))) * invH2;
-          const T* pp = psi + ((long long)t * N * N + l) * 2 * kmax;
-          const double* u = uc + (long long)s * Nt + coff[i];
-          double ax = 0.0, ay = 0.0;
-          for (int a = 0; a < k; ++a) {
-            ax = fma((double)pp[a], u[a], ax);
-            ay = fma((double)pp[kmax + a], u[a], ay);
-          }
-          zx = fma(chi, ax, zx);
-          zy = fma(chi, ay, zy);
+  const int nseq = 4 * NL;   // 2 directions x NL lines x 2 halves
+  auto src = [&](int m) -> const T* {
+    const int line = m >> 1, half = m & 1;
+    if (line < NL) return fwd + (((long long)type * NL + line) * 2 + half) * blk;
+    const int k = NL - 1 - (line - NL);
+    return bwd + (((long long)type * NL + k) * 2 + half) * blk;
+  };
+  if (threadIdx.x == 0)
+    for (int b = 0; b < NBUF && b < nseq; ++b) {
+      mbar_expect_tx(&bars[b], bytes);
+      bulk_g2s(stg + b * blk, src(b), bytes, &bars[b]);
+    }
+  uint32_t phase[2] = {0u, 0u};
+  // thread roles: a pair of rows (rl, rl + hp) of the half block, reduction part pp of S
+  const int t = threadIdx.x;
+  const int pp = t % S, rl = t / S;
+  const int hp = (hrows + 1) >> 1;
+  // zero the padding rows of the vectors once (nb..nbs-1) so the inner loops need no bounds
+  for (int q = nb * R + threadIdx.x; q < nbs * R; q += blockDim.x) {
+    vb[q] = T(0);
+    prev[q] = T(0);
+    cur[q] = T(0);
+  }
+  int m = 0;
+  for (int ls = 0; ls < 2 * NL; ++ls) {
+    const bool fw = ls < NL;
+    const int k = fw ? ls : NL - 1 - (ls - NL);
+    const bool has_prev = fw ? (k > 0) : (k < NL - 1);
+    // input vector of the line
+    if (fw) {
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) {
+        const int c = q / R, col = q % R;
+        const int p = col / nsys, s = col % nsys;
+        T v = T(0);
+        if (p < cnt && col < cnt * nsys && fr[(long long)k * nb + c]) {
+          const int ia = s_node[p];
+          const int I = ia % (ncx + 1), J = ia / (ncx + 1);
+          const int x = (I - 1) * H + (c >> 1), y = (J - 1) * H + k;
+          if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
+            v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
         }
-        if (part != 1) {
-          const int lb = y - (J - 1) * H, la = x - (I - 1) * H;
-          const int col = agg_slot[i] * nsys + s;
-          const long long base = (((long long)agg_group[i] * NP + lb) * R + col) * nbP + 2 * la;
-          zx += (double)Xg[base];
-          zy += (double)Xg[base + 1];
+        vb[q] = v;
+      }
+    } else {
+      const T* yk = X + (long long)k * nb * R;
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[q] = yk[q];
+    }
+    __syncthreads();
+    for (int half = 0; half < 2; ++half, ++m) {
+      const int b = m % NBUF;
+      if (threadIdx.x == 0 && !s_abort && !mbar_wait(&bars[b], phase[b])) {
+        s_abort = 1;
+        atomicExch(err, (int)MSTOPO_TIMEOUT);
+      }
+      phase[b] ^= 1u;
+      __syncthreads();
+      const T* A = stg + b * blk;
+      const T* Bm = A + (long long)hrows * nbs;
+      const int ra = rl, rb = rl + hp;                  // local rows of the pair
+      const bool va = ra < hp && half * hrows + ra < nb;
+      const bool vbr = va && rb < hrows && half * hrows + rb < nb;
+      const int ia = half * hrows + ra, ib = half * hrows + rb;
+      T acc0[R], acc1[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) { acc0[j] = T(0); acc1[j] = T(0); }
+      if (va) {
+        // lanes of a row pair take every S-th column (conflict-free shared loads of both the
+        // matrix rows and the vectors); the factor is zero outside each row's triangle
+        const T* Ar0 = A + (long long)ra * nbs;
+        const T* Ar1 = A + (long long)(vbr ? rb : ra) * nbs;
+        const int hi = vbr ? ib : ia;
+        const int c0 = fw ? 0 : ia, c1 = fw ? hi + 1 : nb;
+#pragma unroll 4
+        for (int c = c0 + pp; c < c1; c += S) {
+          const T a0 = Ar0[c], a1 = Ar1[c];
+          T v[R];
+          load_vec<T, R>(vb + c * R, v);
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            acc0[j] = fma(a0, v[j], acc0[j]);
+            acc1[j] = fma(a1, v[j], acc1[j]);
+          }
+        }
+        if (has_prev) {
+          const T* Br0 = Bm + (long long)ra * nbs;
+          const T* Br1 = Bm + (long long)(vbr ? rb : ra) * nbs;
+#pragma unroll 4
+          for (int c = pp; c < nb; c += S) {
+            const T a0 = Br0[c], a1 = Br1[c];
+            T v[R];
+            load_vec<T, R>(prev + c * R, v);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              acc0[j] = fma(-a0, v[j], acc0[j]);
+              acc1[j] = fma(-a1, v[j], acc1[j]);
+            }
+          }
         }
       }
-    const uint8_t f = nmask[node];
-    z[s * stride + 2 * node] = (f & 1) ? T(0) : (T)zx;
-    z[s * stride + 2 * node + 1] = (f & 2) ? T(0) : (T)zy;
+#pragma unroll
+      for (int o = 1; o < S; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          acc0[j] += __shfl_xor_sync(0xffffffffu, acc0[j], o);
+          acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], o);
+        }
+      if (pp == 0) {
+        if (va) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) cur[ia * R + j] = acc0[j];
+        }
+        if (vbr) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) cur[ib * R + j] = acc1[j];
+        }
+      }
+      __syncthreads();   // block b consumed: refill it
+      if (threadIdx.x == 0 && !s_abort && m + NBUF < nseq) {
+        mbar_expect_tx(&bars[b], bytes);
+        bulk_g2s(stg + b * blk, src(m + NBUF), bytes, &bars[b]);
+      }
+    }
+    // publish the line: forward y_k -> work buffer [nb][R]; backward x_k -> [R][nb]
+    T* Xk = X + (long long)k * nb * R;
+    if (fw) {
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[q];
+    } else {
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q % nb) * R + q / nb];
+    }
+    // the result becomes the previous-line vector
+    T* tmp = prev; prev = cur; cur = tmp;
+    __syncthreads();
+  }
+}
+
+// z(node) = sum over the agglomerates whose box contains the node of
+//           chi_i psi_i uc_i  (coarse part)  +  patch solution of omega_i at the node.
+// One thread per node (2D grid: x fastest), arithmetic in T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_combine(
+    T* __restrict__ z, long long stride, int nsys, int nelx, int nely, int H, int ncx, int ncy,
+    const int* __restrict__ type_of, const int* __restrict__ kept, const int* __restrict__ coff,
+    const T* __restrict__ psi, int kmax, const double* __restrict__ uc, int Nt,
+    const int* __restrict__ agg_group, const int* __restrict__ agg_slot, const T* __restrict__ Xg,
+    int R, const uint8_t* __restrict__ nmask, int part) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int s = blockIdx.z;
+  if (x > nelx) return;
+  const int N = 2 * H + 1, nbP = 2 * N;
+  const T invH2 = T(1) / (T)(H * H);
+  T zx = T(0), zy = T(0);
+  const int Ib = x / H, Jb = y / H;
+  for (int J = max(Jb - 1, 0); J <= min(Jb + 1, ncy); ++J) {
+    const int dyj = abs(y - J * H);
+    if (dyj > H) continue;
+    for (int I = max(Ib - 1, 0); I <= min(Ib + 1, ncx); ++I) {
+      const int dxi = abs(x - I * H);
+      if (dxi > H) continue;
+      const int i = J * (ncx + 1) + I;
+      const int lb = y - (J - 1) * H, la = x - (I - 1) * H;
+      const long long l = (long long)lb * N + la;
+      if (part != 2 && dxi < H && dyj < H) {
+        const int t = type_of[i], k = kept[t];
+        const T chi = (T)((H - dxi) * (H - dyj)) * invH2;
+        const T* pp = psi + ((long long)t * N * N + l) * 2 * kmax;
+        const double* u = uc + (long long)s * Nt + coff[i];
+        T ax = T(0), ay = T(0);
+        for (int a = 0; a < k; ++a) {
+          const T ua = (T)u[a];
+          ax = fma(pp[a], ua, ax);
+          ay = fma(pp[kmax + a], ua, ay);
+        }
+        zx = fma(chi, ax, zx);
+        zy = fma(chi, ay, zy);
+      }
+      if (part != 1) {
+        const int col = agg_slot[i] * nsys + s;
+        const long long base = (((long long)agg_group[i] * N + lb) * R + col) * nbP + 2 * la;
+        zx += Xg[base];
+        zy += Xg[base + 1];
+      }
+    }
+  }
+  const long long node = (long long)y * (nelx + 1) + x;
+  const uint8_t f = nmask[node];
+  z[s * stride + 2 * node] = (f & 1) ? T(0) : zx;
+  z[s * stride + 2 * node + 1] = (f & 2) ? T(0) : zy;
+}
+
+// W_k = Linv_k C_{k-1} (k >= 1) and V_k = Linv_k^T C_k^T (k <= NL-2), FP64, one CTA per
+// (type, line, which); zero where undefined.
+__global__ void __launch_bounds__(PC_THREADS) k_patch_wv(const double* __restrict__ Linv,
+                                                         const double* __restrict__ C,
+                                                         double* __restrict__ W,
+                                                         double* __restrict__ V, int nb, int NL) {
+  const int type = blockIdx.x, k = blockIdx.y, which = blockIdx.z;
+  const long long nn = (long long)nb * nb;
+  const double* Lk = Linv + ((long long)type * NL + k) * nn;
+  double* out = (which == 0 ? W : V) + ((long long)type * NL + k) * nn;
+  const bool defined = which == 0 ? (k >= 1) : (k <= NL - 2);
+  const double* Cm = defined ? C + ((long long)type * (NL - 1) + (which == 0 ? k - 1 : k)) * nn : nullptr;
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    double s = 0.0;
+    if (defined) {
+      if (which == 0)
+        for (int l = 0; l <= i; ++l) s = fma(Lk[i * nb + l], Cm[l * nb + j], s);
+      else
+        for (int l = i; l < nb; ++l) s = fma(Lk[l * nb + i], Cm[j * nb + l], s);
+    }
+    out[t] = s;
+  }
+}
+
+// Solve-ready layout for the patch solve: per (type, line, row half) one contiguous stage
+// block of two row slices (rpc rows, row stride nbs, zero padded):
+// forward [Linv_k rows | W_k rows], backward [Linv_k^T rows | V_k rows].
+__global__ void k_patch_pack(const double* __restrict__ Linv, const double* __restrict__ W,
+                             const double* __restrict__ V, int nb, int NL, int rpc, int nbs,
+                             double* __restrict__ f64, double* __restrict__ b64,
+                             float* __restrict__ f32, float* __restrict__ b32) {
+  const int type = blockIdx.x, k = blockIdx.y, bw = blockIdx.z;
+  const long long nn = (long long)nb * nb;
+  const long long blk = 2LL * rpc * nbs;
+  const double* Lk = Linv + ((long long)type * NL + k) * nn;
+  const double* Mk = (bw ? V : W) + ((long long)type * NL + k) * nn;
+  for (long long t = threadIdx.x; t < (long long)PATCH_HALVES * blk; t += blockDim.x) {
+    const int rank = t / blk;
+    const long long u = t % blk;
+    const int half = u / ((long long)rpc * nbs);
+    const int r = (u / nbs) % rpc, c = u % nbs;
+    const int row = rank * rpc + r;
+    double v = 0.0;
+    if (row < nb && c < nb) {
+      if (half == 0) v = bw ? Lk[(long long)c * nb + row] : Lk[(long long)row * nb + c];
+      else v = Mk[(long long)row * nb + c];
+    }
+    const long long o = (((long long)type * NL + k) * PATCH_HALVES) * blk + t;
+    if (bw) { b64[o] = v; b32[o] = (float)v; }
+    else { f64[o] = v; f32[o] = (float)v; }
   }
 }
 
@@ -782,6 +998,7 @@ void precond_free(Precond& pc) {
   dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff); dfree(pc.d_perm);
   dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count);
   dfree(pc.d_pfree); dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
+  dfree(pc.d_pf64); dfree(pc.d_pb64); dfree(pc.d_pf32); dfree(pc.d_pb32);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
   dfree(pc.d_Kc); dfree(pc.d_Kcinv); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
   dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
@@ -931,12 +1148,32 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
                                        pc.d_pC64, pS, d_st);
   CKB(cudaGetLastError());
   CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CKB(cudaMalloc(&pc.d_pLinv32, (size_t)T * NP * nnP * 4));
-  CKB(cudaMalloc(&pc.d_pC32, (size_t)T * (NP - 1) * nnP * 4));
-  note_launch(), k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pLinv64, pc.d_pLinv32, (long long)T * NP * nnP);
-  note_launch(), k_d2f_copy<<<608, 256, 0, s>>>(pc.d_pC64, pc.d_pC32, (long long)T * (NP - 1) * nnP);
-  CKB(cudaGetLastError());
-  CKB(cudaStreamSynchronize(s));
+  // W_k, V_k and the packed stage blocks (FP64 and FP32) for the cluster patch solve
+  pc.rpc = (nbP + PATCH_HALVES - 1) / PATCH_HALVES;
+  pc.nbs = (nbP + 3) / 4 * 4;
+  {
+    double *dW, *dV;
+    CKB(cudaMalloc(&dW, (size_t)T * NP * nnP * 8));
+    CKB(cudaMalloc(&dV, (size_t)T * NP * nnP * 8));
+    note_launch(), k_patch_wv<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pc.d_pLinv64, pc.d_pC64, dW, dV, nbP, NP);
+    CKB(cudaGetLastError());
+    const size_t pk = (size_t)T * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
+    CKB(cudaMalloc(&pc.d_pf64, pk * 8));
+    CKB(cudaMalloc(&pc.d_pb64, pk * 8));
+    CKB(cudaMalloc(&pc.d_pf32, pk * 4));
+    CKB(cudaMalloc(&pc.d_pb32, pk * 4));
+    note_launch(), k_patch_pack<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pc.d_pLinv64, dW, dV, nbP, NP, pc.rpc,
+                                                                    pc.nbs, pc.d_pf64, pc.d_pb64,
+                                                                    pc.d_pf32, pc.d_pb32);
+    CKB(cudaGetLastError());
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(dW);
+    cudaFree(dV);
+    cudaFree(pc.d_pLinv64);
+    cudaFree(pc.d_pC64);
+    pc.d_pLinv64 = nullptr;
+    pc.d_pC64 = nullptr;
+  }
   cudaFree(pA); cudaFree(pB); cudaFree(pS); cudaFree(d_rep);
   for (int t = 0; t < T; ++t)
     if (fst[t]) {
@@ -1005,12 +1242,16 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   std::vector<std::vector<int>> by_type(T);
   for (int i = 0; i < pc.Nc; ++i) by_type[pc.h_type_of_agg[i]].push_back(i);
   std::vector<int> perm, gt, gf, gc, agg_group(pc.Nc), agg_slot(pc.Nc);
+  // four patches per CTA keeps ~one CTA per SM at the 1024x512 size; more columns per CTA
+  // would amortise the block streaming further but leave SMs idle
+  const int P = std::max(1, std::min(PATCH_GROUP, PATCH_COLS / std::max(1, h->n_eta)));
+  pc.patches_per_group = P;
   for (int t = 0; t < T; ++t)
-    for (size_t b = 0; b < by_type[t].size(); b += PC_GROUP) {
+    for (size_t b = 0; b < by_type[t].size(); b += P) {
       int g = (int)gt.size();
       gt.push_back(t);
       gf.push_back((int)perm.size());
-      int c = (int)std::min<size_t>(PC_GROUP, by_type[t].size() - b);
+      int c = (int)std::min<size_t>(P, by_type[t].size() - b);
       gc.push_back(c);
       for (int p = 0; p < c; ++p) {
         int i = by_type[t][b + p];
@@ -1033,7 +1274,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMemcpyAsync(agg_slot_ptr(pc), agg_slot.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
-  const size_t xg = (size_t)pc.n_groups * nP * PC_GROUP * MSTOPO_MAX_SYS;
+  const size_t xg = (size_t)pc.n_groups * nP * PATCH_COLS;
   CKB(cudaMalloc(&pc.d_zp32, xg * 4));
   CKB(cudaMalloc(&pc.d_zp64, xg * 8));
   CKB(cudaEventRecord(ev[5], s));
@@ -1060,22 +1301,33 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   return MSTOPO_OK;
 }
 
-template <typename T, int R>
-static cudaError_t launch_patch(mstopo_handle* h, const T* r, int nsys, size_t sm, const T* Linv,
-                                const T* C, T* Xg) {
+template <typename T, int Q>
+static cudaError_t launch_patch(mstopo_handle* h, const T* r, int nsys, const T* fwd, const T* bwd,
+                                T* Xg) {
   Precond& pc = h->pc;
-  cudaError_t e = cudaFuncSetAttribute(k_patch_solve<T, R>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  note_launch(), k_patch_solve<T, R><<<pc.n_groups, SOLVE_THREADS, sm, h->s>>>(
+  const int nb = pc.nbP, R = 4 * Q;
+  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
+  const long long blk = 2LL * pc.rpc * pc.nbs;
+  const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * R) * sizeof(T);
+  (void)nb;
+  // the shared-memory limit is raised once per instantiation (never inside a graph capture)
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_patch_solve_f<T, Q, NBUF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
+  note_launch(), k_patch_solve_f<T, Q, NBUF><<<pc.n_groups, PATCH_THREADS, sm, h->s>>>(
       r, h->n_dof, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_first,
-      pc.d_grp_count, pc.d_perm, pc.d_pfree, Linv, C, Xg, h->d_flag + 1);
+      pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg, h->d_flag + 1);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int part,
-                              const T* psi, const T* Linv, const T* C, T* Xg) {
+                              const T* psi, const T* fwd, const T* bwd, T* Xg) {
   Precond& pc = h->pc;
   cudaStream_t s = h->s;
   const long long n = h->n_dof;
@@ -1087,34 +1339,34 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int 
     note_launch(), k_coarse_gemv<<<cdiv((long long)pc.Nt * 32, 256), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, nsys);
     prof_end(h->prof, PROF_COARSE, pa, s);
   }
+  int Rcols = 4;
   if (part != 1) {
-    const int nbP = pc.nbP, R = PC_GROUP * nsys;
-    const int nbuf = sizeof(T) == 4 ? 2 : 1;
-    size_t sm = ((size_t)nbuf * nbP * nbP + 2 * (size_t)nbP * R) * sizeof(T);
+    const int Q = (pc.patches_per_group * nsys + 3) / 4;
+    Rcols = 4 * Q;
     cudaEvent_t pa = prof_begin(h->prof, s);
     cudaError_t e;
-    switch (R) {
-      case 4: e = launch_patch<T, 4>(h, r, nsys, sm, Linv, C, Xg); break;
-      case 8: e = launch_patch<T, 8>(h, r, nsys, sm, Linv, C, Xg); break;
-      case 12: e = launch_patch<T, 12>(h, r, nsys, sm, Linv, C, Xg); break;
-      default: e = launch_patch<T, 16>(h, r, nsys, sm, Linv, C, Xg); break;
+    switch (Q) {
+      case 1: e = launch_patch<T, 1>(h, r, nsys, fwd, bwd, Xg); break;
+      case 2: e = launch_patch<T, 2>(h, r, nsys, fwd, bwd, Xg); break;
+      case 3: e = launch_patch<T, 3>(h, r, nsys, fwd, bwd, Xg); break;
+      default: e = launch_patch<T, 4>(h, r, nsys, fwd, bwd, Xg); break;
     }
     if (e != cudaSuccess) return e;
     prof_end(h->prof, PROF_PATCH, pa, s);
   }
-  note_launch(), k_combine<T><<<dim3(608, nsys), 256, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
+  note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
                                                pc.d_uc, pc.Nt, agg_group_ptr(pc), agg_slot_ptr(pc), Xg,
-                                               h->d_nmask, part);
+                                               Rcols, h->d_nmask, part);
   return cudaGetLastError();
 }
 
 cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int nsys, int part) {
   Precond& pc = h->pc;
-  return apply_impl<double>(h, r, z, nsys, part, pc.d_psi64, pc.d_pLinv64, pc.d_pC64, pc.d_zp64);
+  return apply_impl<double>(h, r, z, nsys, part, pc.d_psi64, pc.d_pf64, pc.d_pb64, pc.d_zp64);
 }
 
 cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int nsys, int part) {
   Precond& pc = h->pc;
-  return apply_impl<float>(h, r, z, nsys, part, pc.d_psi32, pc.d_pLinv32, pc.d_pC32, pc.d_zp32);
+  return apply_impl<float>(h, r, z, nsys, part, pc.d_psi32, pc.d_pf32, pc.d_pb32, pc.d_zp32);
 }
