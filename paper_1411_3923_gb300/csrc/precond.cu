@@ -29,10 +29,15 @@
 #include <map>
 #include <utility>
 
+#include <cooperative_groups.h>
+
 #include "blocktri.cuh"
+
+namespace cg = cooperative_groups;
 
 #define PC_THREADS 256
 #define SOLVE_THREADS 320   // 160 rows x 2 threads per pass covers nb = 2(2H+1) up to H = 39
+#define EIG_CL 4            // CTAs per agglomerate type in the eigen-solve (subspace columns split)
 #define PATCH_HALVES 2      // row halves of every line in the patch solve
 #define PATCH_S 8           // threads sharing one row pair in the patch solve
 #define PATCH_THREADS 288   // >= ceil(hrows / 2) * PATCH_S = 33 * 8 for H = 32 (warp multiple)
@@ -152,13 +157,16 @@ __global__ void k_assemble_box(const double* __restrict__ E, const uint8_t* __re
 }
 
 // ------------------------------------------------------------------------ factorisation
+// systems [0, split) are factorised with diagonal shift s_lo, the others with s_hi
 __global__ void k_bt_factor(const double* __restrict__ A, const double* __restrict__ B,
-                            const uint8_t* __restrict__ freem, double shift, int nb, int NL,
-                            double* __restrict__ Linv, double* __restrict__ C,
-                            double* __restrict__ Swork, int* __restrict__ status) {
+                            const uint8_t* __restrict__ freem, double s_lo, double s_hi,
+                            int split, int nb, int NL, double* __restrict__ Linv,
+                            double* __restrict__ C, double* __restrict__ Swork,
+                            int* __restrict__ status) {
   __shared__ int sh_fail;
   const long long nn = (long long)nb * nb;
   const int sys = blockIdx.x;
+  const double shift = sys < split ? s_lo : s_hi;
   int f = bt_factor(A + sys * NL * nn, B + sys * (NL - 1) * nn,
                     freem ? freem + (long long)sys * NL * nb : nullptr, shift, nb, NL,
                     Linv + sys * NL * nn, C + sys * (NL - 1) * nn, Swork + sys * nn, &sh_fail);
@@ -285,21 +293,23 @@ struct EigArgs {
   const double* E; const uint8_t* nmask; int nelx, nely, H, ncx;
   const int* rep; const double* A; const uint8_t* freem;
   const double* Linv; const double* C;     // factor of K_w + shift diag(K_w)
-  double* X; double* Y; double* KY;        // [T][NL][nb][q]
+  double* X; double* Y; double* KY; double* KX;   // [T][NL][nb][q]
+  double* Ysc;                             // [T][EIG_CL][NL*nb][q/EIG_CL]
+  double* GM; double* resg;                // [T][2][q][q], [T][q]
   int q, kmax; double lam_thresh;
   double* lambda; int* kept; double* res; int* sweeps;
   int* err;
   K0P K0;
 };
 
-// y = K_w x on the agglomerate box (elements of the agglomerate only), R columns,
-// [N][nb][R] layout; zero on non-free DOFs.
-__device__ void box_apply(const EigArgs& a, int I, int J, const uint8_t* freem, const double* x,
-                          double* y, int R) {
+// y = K_w x on the agglomerate box (elements of the agglomerate only) for the columns
+// [j0, j0 + nc) of [N][nb][R]-laid-out vectors; zero on non-free DOFs.
+__device__ void box_apply_cols(const EigArgs& a, int I, int J, const uint8_t* freem,
+                               const double* x, double* y, int R, int j0, int nc) {
   const int H = a.H, N = 2 * H + 1, nb = 2 * N;
   const int ox = (I - 1) * H, oy = (J - 1) * H;
-  for (int t = threadIdx.x; t < N * nb * R; t += blockDim.x) {
-    const int r = t % R, dof = t / R;
+  for (int t = threadIdx.x; t < N * nb * nc; t += blockDim.x) {
+    const int r = j0 + t % nc, dof = t / nc;
     const int line = dof / nb, rr = dof % nb, na = rr >> 1, cr = rr & 1;
     double s = 0.0;
     if (freem[dof]) {
@@ -321,16 +331,23 @@ __device__ void box_apply(const EigArgs& a, int I, int J, const uint8_t* freem, 
         s = fma(Ee, es, s);
       }
     }
-    y[t] = s;
+    y[(long long)dof * R + r] = s;
   }
 }
 
+// One 4-CTA cluster per agglomerate type.  CTA rank r owns the subspace columns
+// [r*QC, (r+1)*QC): it applies the shifted inverse and K_w to them; the q x q projections
+// G = Y^T K Y, M = Y^T D Y are assembled from all columns (global memory, cluster barriers)
+// and every CTA performs the same small Rayleigh-Ritz step.
 template <int Q>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
-  extern __shared__ double smem[];
-  const int type = blockIdx.x;
-  const int H = a.H, N = 2 * H + 1, nb = 2 * N;
+__global__ void __cluster_dims__(EIG_CL, 1, 1) __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
+  constexpr int QC = Q / EIG_CL;
   constexpr int q = Q;
+  extern __shared__ double smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int type = blockIdx.x / EIG_CL;
+  const int H = a.H, N = 2 * H + 1, nb = 2 * N;
   const long long n = (long long)N * nb, nn = (long long)nb * nb;
   const int ia = a.rep[type];
   const int I = ia % (a.ncx + 1), J = ia / (a.ncx + 1);
@@ -341,54 +358,67 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
   double* X = a.X + (long long)type * n * q;
   double* Y = a.Y + (long long)type * n * q;
   double* KY = a.KY + (long long)type * n * q;
+  double* KX = a.KX + (long long)type * n * q;
+  double* Yc = a.Ysc + ((long long)type * EIG_CL + rank) * n * QC;   // my columns, contiguous
+  double* GMg = a.GM + (long long)type * 2 * q * q;                    // G then M (global)
+  double* resg = a.resg + (long long)type * q;
   double* stage = smem;                    // nn
-  double* t0 = stage + nn;                 // nb*q
-  double* t1 = t0 + nb * q;                // nb*q
-  double* G = t1 + nb * q;                 // q*q
+  double* t0 = stage + nn;                 // nb*QC
+  double* t1 = t0 + nb * QC;               // nb*QC
+  double* G = t1 + nb * QC;                // q*q
   double* M = G + q * q;                   // q*q
   double* W = M + q * q;                   // q*q
   double* scr = W + q * q;                 // 3 q*q
   double* theta = scr + 3 * q * q;         // q
-  double* res = theta + q;                 // q
   __shared__ int s_done, s_fail;
   __shared__ __align__(8) uint64_t s_bars[2];
-  // D = diag(K_w) per DOF (from the assembled diagonal blocks)
+  const int j0 = rank * QC;
   auto Dof = [&](long long dof) -> double {
     long long line = dof / nb, r = dof % nb;
     return Ak[line * nn + r * nb + r];
   };
-  // deterministic start block, zero on non-free DOFs
-  for (long long t = threadIdx.x; t < n * q; t += blockDim.x) {
-    long long dof = t / q;
-    unsigned long long z = mix64((unsigned long long)t * 0x9E3779B97F4A7C15ull + 12345u);
-    X[t] = fr[dof] ? ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5) : 0.0;
+  // deterministic start block, zero on non-free DOFs (same values as a single-CTA start)
+  for (long long t = threadIdx.x; t < n * QC; t += blockDim.x) {
+    const long long dof = t / QC;
+    const int j = j0 + (int)(t % QC);
+    const long long g = dof * q + j;
+    unsigned long long z = mix64((unsigned long long)g * 0x9E3779B97F4A7C15ull + 12345u);
+    X[g] = fr[dof] ? ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5) : 0.0;
   }
   if (threadIdx.x == 0) { s_done = 0; s_fail = 0; }
-  __syncthreads();
+  cluster.sync();
   int sweep = 0;
   for (; sweep < EIG_MAX_SWEEPS && !s_done; ++sweep) {
-    // Y = (K + s D)^-1 D X
-    for (long long t = threadIdx.x; t < n * q; t += blockDim.x) Y[t] = Dof(t / q) * X[t] * fr[t / q];
+    // my columns: Y = (K + s D)^-1 D X
+    for (long long t = threadIdx.x; t < n * QC; t += blockDim.x) {
+      const long long dof = t / QC;
+      Yc[t] = Dof(dof) * X[dof * q + j0 + t % QC] * fr[dof];
+    }
     __syncthreads();
-    bt_solve_bulk<double, 1, Q, false>(Linv, C, nb, N, Y, stage, t0, t1, s_bars, a.err);
-    for (long long t = threadIdx.x; t < n * q; t += blockDim.x) if (!fr[t / q]) Y[t] = 0.0;
+    bt_solve_bulk<double, 1, QC, false>(Linv, C, nb, N, Yc, stage, t0, t1, s_bars, a.err);
+    for (long long t = threadIdx.x; t < n * QC; t += blockDim.x) {
+      const long long dof = t / QC;
+      Y[dof * q + j0 + t % QC] = fr[dof] ? Yc[t] : 0.0;
+    }
     __syncthreads();
-    box_apply(a, I, J, fr, Y, KY, q);
-    __syncthreads();
-    // G = Y^T K Y, M = Y^T D Y
-    for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
-      int i = t / q, j = t % q;
+    // my columns: KY = K_w Y
+    box_apply_cols(a, I, J, fr, Y, KY, q, j0, QC);
+    cluster.sync();
+    // rows of G and M for my columns
+    for (int t = threadIdx.x; t < QC * q; t += blockDim.x) {
+      const int i = j0 + t / q, j = t % q;
       double g = 0.0, m = 0.0;
       for (long long d = 0; d < n; ++d) {
-        double yi = Y[d * q + i];
+        const double yi = Y[d * q + i];
         g = fma(yi, KY[d * q + j], g);
         m = fma(yi * Dof(d), Y[d * q + j], m);
       }
-      G[t] = g;
-      M[t] = m;
+      GMg[i * q + j] = g;
+      GMg[q * q + i * q + j] = m;
     }
-    __syncthreads();
+    cluster.sync();
     if (threadIdx.x == 0) {
+      for (int t = 0; t < q * q; ++t) { G[t] = GMg[t]; M[t] = GMg[q * q + t]; }
       for (int i = 0; i < q; ++i)
         for (int j = 0; j < i; ++j) {
           double g = 0.5 * (G[i * q + j] + G[j * q + i]), m = 0.5 * (M[i * q + j] + M[j * q + i]);
@@ -398,40 +428,54 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
       if (rayleigh_ritz(G, M, q, theta, W, scr)) s_fail = 1;
     }
     __syncthreads();
-    if (s_fail) break;
-    // X = Y W, KX (in KY) = KY W, row by row
+    // my columns: X = Y W, KX = KY W
     for (long long d = threadIdx.x; d < n; d += blockDim.x) {
-      double yr[2 * MSTOPO_MAX_EIG], kr[2 * MSTOPO_MAX_EIG];
+      double yr[Q], kr[Q];
+#pragma unroll
       for (int i = 0; i < q; ++i) { yr[i] = Y[d * q + i]; kr[i] = KY[d * q + i]; }
-      for (int j = 0; j < q; ++j) {
+#pragma unroll
+      for (int jj = 0; jj < QC; ++jj) {
+        const int j = j0 + jj;
         double xs = 0.0, ks = 0.0;
+#pragma unroll
         for (int i = 0; i < q; ++i) { xs = fma(yr[i], W[i * q + j], xs); ks = fma(kr[i], W[i * q + j], ks); }
         X[d * q + j] = xs;
-        KY[d * q + j] = ks;
+        KX[d * q + j] = ks;
       }
     }
     __syncthreads();
-    // residual norms of the wanted pairs: ||K x - theta D x||_{D^-1}
-    const int kw = a.kmax;
-    for (int j = threadIdx.x; j < kw; j += blockDim.x) {
-      double s = 0.0;
-      for (long long d = 0; d < n; ++d) {
+    // residual norms of the wanted pairs among my columns: ||K x - theta D x||_{D^-1}
+    for (int jj = 0; jj < QC; ++jj) {
+      const int j = j0 + jj;
+      if (j >= a.kmax) break;
+      double sacc = 0.0;
+      for (long long d = threadIdx.x; d < n; d += blockDim.x) {
         if (!fr[d]) continue;
-        double Dd = Dof(d);
-        double v = KY[d * q + j] - theta[j] * Dd * X[d * q + j];
-        s = fma(v, v / Dd, s);
+        const double Dd = Dof(d);
+        const double v = KX[d * q + j] - theta[j] * Dd * X[d * q + j];
+        sacc = fma(v, v / Dd, sacc);
       }
-      res[j] = sqrt(s);
+      // block reduction into resg[j]
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+      __shared__ double red[SOLVE_THREADS / 32];
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sacc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        resg[j] = sqrt(tot);
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    cluster.sync();
     if (threadIdx.x == 0) {
       double m = 0.0;
-      for (int j = 0; j < kw; ++j) m = fmax(m, res[j]);
-      if (m <= EIG_TOL) s_done = 1;
+      for (int j = 0; j < a.kmax; ++j) m = fmax(m, resg[j]);
+      if (m <= EIG_TOL || s_fail) s_done = 1;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (rank == 0 && threadIdx.x == 0) {
     int kept = a.kmax;
     if (a.lam_thresh > 0.0) {
       kept = 0;
@@ -441,7 +485,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_eigen(EigArgs a) {
     double m = 0.0;
     for (int j = 0; j < a.kmax; ++j) {
       a.lambda[type * MSTOPO_MAX_EIG + j] = theta[j];
-      if (j < kept) m = fmax(m, res[j]);
+      if (j < kept) m = fmax(m, resg[j]);
     }
     a.kept[type] = s_fail ? -1 : kept;
     a.res[type] = m;
@@ -453,7 +497,7 @@ template <int Q>
 static cudaError_t launch_eigen_q(int T, size_t esm, cudaStream_t s, const EigArgs& ea) {
   cudaError_t e = cudaFuncSetAttribute(k_eigen<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
   if (e != cudaSuccess) return e;
-  note_launch(), k_eigen<Q><<<T, SOLVE_THREADS, esm, s>>>(ea);
+  note_launch(), k_eigen<Q><<<T * EIG_CL, SOLVE_THREADS, esm, s>>>(ea);
   return cudaGetLastError();
 }
 
@@ -1058,29 +1102,47 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMemcpyAsync(pc.d_type_of_agg, pc.h_type_of_agg.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaEventRecord(ev[1], s));
 
-  // 2. agglomerate matrices, shifted factor, eigen-solve
-  const int NA = pc.NA, nbA = pc.nbA;
+  // 2. agglomerate (Neumann, for the eigenproblem) and patch (artificial boundary Dirichlet)
+  //    matrices of every type, both factorised in one launch: systems [0,T) are the shifted
+  //    agglomerate matrices K_w + s diag(K_w), systems [T,2T) the patch matrices
+  const int NA = pc.NA, nbA = pc.nbA, NP = pc.NP, nbP = pc.nbP;
   const long long nnA = (long long)nbA * nbA, nA = (long long)NA * nbA;
+  const long long nnP = nnA, nP = nA;
   // subspace dimension: 2k + 4 rounded up to a multiple of 4 (compile-time variants)
   const int q = std::min(((2 * pc.kmax + 4) + 3) / 4 * 4, 2 * MSTOPO_MAX_EIG);
-  double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY;
+  double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY, *dKX, *dYsc, *dGM, *dres;
   uint8_t* dfree_;
   int* d_st;
-  CKB(cudaMalloc(&dA, (size_t)T * NA * nnA * 8));
-  CKB(cudaMalloc(&dB, (size_t)T * (NA - 1) * nnA * 8));
-  CKB(cudaMalloc(&dLi, (size_t)T * NA * nnA * 8));
-  CKB(cudaMalloc(&dC, (size_t)T * (NA - 1) * nnA * 8));
-  CKB(cudaMalloc(&dS, (size_t)T * nnA * 8));
+  CKB(cudaMalloc(&dA, (size_t)2 * T * NA * nnA * 8));
+  CKB(cudaMalloc(&dB, (size_t)2 * T * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dLi, (size_t)2 * T * NA * nnA * 8));
+  CKB(cudaMalloc(&dC, (size_t)2 * T * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dS, (size_t)2 * T * nnA * 8));
   CKB(cudaMalloc(&dfree_, (size_t)T * nA));
-  CKB(cudaMalloc(&d_st, (size_t)std::max(T, 1) * sizeof(int)));
-  CKB(cudaMalloc(&dX, (size_t)T * nA * q * 8));
-  CKB(cudaMalloc(&dY, (size_t)T * nA * q * 8));
-  CKB(cudaMalloc(&dKY, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&pc.d_pfree, (size_t)T * nP));
+  CKB(cudaMalloc(&d_st, (size_t)2 * std::max(T, 1) * sizeof(int)));
   note_launch(), k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
                                                     pc.ncx, 0, K0, dA, dB, dfree_);
   CKB(cudaGetLastError());
-  note_launch(), k_bt_factor<<<T, PC_THREADS, 0, s>>>(dA, dB, dfree_, EIG_SHIFT, nbA, NA, dLi, dC, dS, d_st);
+  note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
+                                                    pc.ncx, 1, K0, dA + (size_t)T * NA * nnA,
+                                                    dB + (size_t)T * (NA - 1) * nnA, pc.d_pfree);
   CKB(cudaGetLastError());
+  // the shift flags need a per-system free mask: agglomerate masks, then patch masks
+  uint8_t* dfree2;
+  CKB(cudaMalloc(&dfree2, (size_t)2 * T * nA));
+  CKB(cudaMemcpyAsync(dfree2, dfree_, (size_t)T * nA, cudaMemcpyDeviceToDevice, s));
+  CKB(cudaMemcpyAsync(dfree2 + (size_t)T * nA, pc.d_pfree, (size_t)T * nP, cudaMemcpyDeviceToDevice, s));
+  note_launch(), k_bt_factor<<<2 * T, PC_THREADS, 0, s>>>(dA, dB, dfree2, EIG_SHIFT, pc.local_shift, T, nbA, NA,
+                                                           dLi, dC, dS, d_st);
+  CKB(cudaGetLastError());
+  CKB(cudaMalloc(&dX, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dY, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dKY, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dKX, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dYsc, (size_t)T * nA * q * 8));
+  CKB(cudaMalloc(&dGM, (size_t)T * 2 * q * q * 8));
+  CKB(cudaMalloc(&dres, (size_t)T * q * 8));
   CKB(cudaMalloc(&pc.d_lambda, (size_t)T * MSTOPO_MAX_EIG * 8));
   CKB(cudaMemsetAsync(pc.d_lambda, 0, (size_t)T * MSTOPO_MAX_EIG * 8, s));
   CKB(cudaMalloc(&pc.d_kept, T * sizeof(int)));
@@ -1089,12 +1151,14 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   EigArgs ea;
   ea.E = E; ea.nmask = h->d_nmask; ea.nelx = h->nelx; ea.nely = h->nely; ea.H = H; ea.ncx = pc.ncx;
   ea.rep = d_rep; ea.A = dA; ea.freem = dfree_; ea.Linv = dLi; ea.C = dC;
-  ea.X = dX; ea.Y = dY; ea.KY = dKY; ea.q = q; ea.kmax = pc.kmax; ea.lam_thresh = h->p.lambda_thresh;
+  ea.X = dX; ea.Y = dY; ea.KY = dKY; ea.KX = dKX; ea.Ysc = dYsc; ea.GM = dGM; ea.resg = dres;
+  ea.q = q; ea.kmax = pc.kmax; ea.lam_thresh = h->p.lambda_thresh;
   ea.lambda = pc.d_lambda; ea.kept = pc.d_kept; ea.res = pc.d_eigres; ea.sweeps = pc.d_eigsweeps;
   ea.K0 = K0;
   ea.err = h->d_flag + 1;
-  size_t esm = (size_t)(nnA + 2 * nbA * q + 6 * q * q + 2 * q) * 8;
-  if (esm > 227 * 1024) {
+  const int qc = q / EIG_CL;
+  size_t esm = (size_t)(nnA + 2 * nbA * qc + 6 * q * q + 2 * q) * 8;
+  if (esm > 225 * 1024) {
     h->err = "n_eig too large for this H: the eigen-solve workspace exceeds shared memory";
     return MSTOPO_INVALID_ARG;
   }
@@ -1104,8 +1168,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     CKB(le);
   }
   CKB(cudaGetLastError());
-  std::vector<int> fst(T);
-  CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  std::vector<int> fst(2 * T);
+  CKB(cudaMemcpyAsync(fst.data(), d_st, 2 * T * sizeof(int), cudaMemcpyDeviceToHost, s));
   pc.h_kept.resize(T);
   CKB(cudaMemcpyAsync(pc.h_kept.data(), pc.d_kept, T * sizeof(int), cudaMemcpyDeviceToHost, s));
   int werr = 0;
@@ -1120,66 +1184,44 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       h->err = "agglomerate eigenproblem failed (non-positive pivot or Rayleigh-Ritz breakdown)";
       return MSTOPO_NOT_SPD;
     }
+    if (fst[T + t]) {
+      h->err = "patch matrix not positive definite";
+      return MSTOPO_NOT_SPD;
+    }
   }
   CKB(cudaMalloc(&pc.d_psi64, (size_t)T * nA * pc.kmax * 8));
   CKB(cudaMalloc(&pc.d_psi32, (size_t)T * nA * pc.kmax * 4));
   note_launch(), k_store_psi<<<dim3(64, T), 256, 0, s>>>(dX, pc.d_kept, (int)nA, q, pc.kmax, pc.d_psi64, pc.d_psi32);
   CKB(cudaGetLastError());
   CKB(cudaEventRecord(ev[2], s));
-  cudaFree(dLi); cudaFree(dC); cudaFree(dS); cudaFree(dX); cudaFree(dY); cudaFree(dKY);
-  cudaFree(dA); cudaFree(dB); cudaFree(dfree_);
 
-  // 3. patch matrices and factors
-  const int NP = pc.NP, nbP = pc.nbP;
-  const long long nnP = (long long)nbP * nbP, nP = (long long)NP * nbP;
-  double *pA, *pB, *pS;
-  uint8_t* pfree;
-  CKB(cudaMalloc(&pA, (size_t)T * NP * nnP * 8));
-  CKB(cudaMalloc(&pB, (size_t)T * (NP - 1) * nnP * 8));
-  CKB(cudaMalloc(&pS, (size_t)T * nnP * 8));
-  CKB(cudaMalloc(&pc.d_pfree, (size_t)T * nP));
-  pfree = pc.d_pfree;
-  CKB(cudaMalloc(&pc.d_pLinv64, (size_t)T * NP * nnP * 8));
-  CKB(cudaMalloc(&pc.d_pC64, (size_t)T * (NP - 1) * nnP * 8));
-  note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
-                                                    pc.ncx, 1, K0, pA, pB, pfree);
-  CKB(cudaGetLastError());
-  note_launch(), k_bt_factor<<<T, PC_THREADS, 0, s>>>(pA, pB, pfree, pc.local_shift, nbP, NP, pc.d_pLinv64,
-                                       pc.d_pC64, pS, d_st);
-  CKB(cudaGetLastError());
-  CKB(cudaMemcpyAsync(fst.data(), d_st, T * sizeof(int), cudaMemcpyDeviceToHost, s));
-  // W_k, V_k and the packed stage blocks (FP64 and FP32) for the cluster patch solve
+  // 3. patch factors: W_k, V_k and the packed stage blocks (FP64 and FP32)
   pc.rpc = (nbP + PATCH_HALVES - 1) / PATCH_HALVES;
   pc.nbs = (nbP + 3) / 4 * 4;
   {
+    const double* pLi = dLi + (size_t)T * NA * nnA;
+    const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
     double *dW, *dV;
     CKB(cudaMalloc(&dW, (size_t)T * NP * nnP * 8));
     CKB(cudaMalloc(&dV, (size_t)T * NP * nnP * 8));
-    note_launch(), k_patch_wv<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pc.d_pLinv64, pc.d_pC64, dW, dV, nbP, NP);
+    note_launch(), k_patch_wv<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
     CKB(cudaGetLastError());
     const size_t pk = (size_t)T * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
     CKB(cudaMalloc(&pc.d_pf64, pk * 8));
     CKB(cudaMalloc(&pc.d_pb64, pk * 8));
     CKB(cudaMalloc(&pc.d_pf32, pk * 4));
     CKB(cudaMalloc(&pc.d_pb32, pk * 4));
-    note_launch(), k_patch_pack<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pc.d_pLinv64, dW, dV, nbP, NP, pc.rpc,
+    note_launch(), k_patch_pack<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pLi, dW, dV, nbP, NP, pc.rpc,
                                                                     pc.nbs, pc.d_pf64, pc.d_pb64,
                                                                     pc.d_pf32, pc.d_pb32);
     CKB(cudaGetLastError());
     CKB(cudaStreamSynchronize(s));
     cudaFree(dW);
     cudaFree(dV);
-    cudaFree(pc.d_pLinv64);
-    cudaFree(pc.d_pC64);
-    pc.d_pLinv64 = nullptr;
-    pc.d_pC64 = nullptr;
   }
-  cudaFree(pA); cudaFree(pB); cudaFree(pS); cudaFree(d_rep);
-  for (int t = 0; t < T; ++t)
-    if (fst[t]) {
-      h->err = "patch matrix not positive definite";
-      return MSTOPO_NOT_SPD;
-    }
+  cudaFree(dLi); cudaFree(dC); cudaFree(dS); cudaFree(dX); cudaFree(dY); cudaFree(dKY);
+  cudaFree(dKX); cudaFree(dYsc); cudaFree(dGM); cudaFree(dres);
+  cudaFree(dA); cudaFree(dB); cudaFree(dfree_); cudaFree(dfree2); cudaFree(d_rep);
   CKB(cudaEventRecord(ev[3], s));
 
   // 4. coarse space: offsets, line mapping, assembly, factor, dense inverse
@@ -1220,7 +1262,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
                                                           cA, cB, nbc);
   CKB(cudaGetLastError());
   // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
-  note_launch(), k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, nbc, NLc, cLi, cC, cS, d_st);
+  note_launch(), k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, 0.0, 1, nbc, NLc, cLi, cC, cS, d_st);
   CKB(cudaGetLastError());
   int cst = 0;
   CKB(cudaMemcpyAsync(&cst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
