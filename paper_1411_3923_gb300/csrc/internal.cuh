@@ -49,12 +49,15 @@ void make_stencil(const double K0[64], StencilCoef<double>& cd, StencilCoef<floa
 
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (each returns the launch status).
+// mask_input: read Dirichlet entries of u as zero (false when u is known to be zero there)
 cudaError_t launch_matvec_f32(const float* u, float* y, const float* E, const uint8_t* nmask,
                               int nelx, int nely, const StencilCoef<float>& c, int nsys,
-                              long long vec_stride, long long e_stride, cudaStream_t s);
+                              long long vec_stride, long long e_stride, cudaStream_t s,
+                              bool mask_input = true);
 cudaError_t launch_matvec_f64(const double* u, double* y, const double* E, const uint8_t* nmask,
                               int nelx, int nely, const StencilCoef<double>& c, int nsys,
-                              long long vec_stride, long long e_stride, cudaStream_t s);
+                              long long vec_stride, long long e_stride, cudaStream_t s,
+                              bool mask_input = true);
 
 // design chain
 cudaError_t launch_filter(const double* rho, double* rho_tilde, double* wsum, int dx, int dy,

@@ -405,7 +405,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
       CK(cudaGetLastError());
       cudaEvent_t pa = prof_begin(h->prof, h->s);
       CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
-                           h->n_el, h->s));
+                           h->n_el, h->s, false));
       prof_end(h->prof, PROF_MATVEC32, pa, h->s);
       note_launch(), k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
     } else {
@@ -413,7 +413,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
       CK(cudaGetLastError());
       cudaEvent_t pa = prof_begin(h->prof, h->s);
       CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
-                           h->n_el, h->s));
+                           h->n_el, h->s, false));
       prof_end(h->prof, PROF_MATVEC64, pa, h->s);
       note_launch(), k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
     }
