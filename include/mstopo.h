@@ -52,6 +52,14 @@ typedef enum {
 } mstopo_precision;
 
 typedef enum {
+  MSTOPO_COARSE_AUTO = 0,      /* explicit inverse up to 4096 coarse unknowns, sweeps above  */
+  MSTOPO_COARSE_DENSE = 1,     /* explicit FP64 inverse of K_c: one GEMV per application     */
+  MSTOPO_COARSE_BLOCKTRI = 2   /* FP64 block Cholesky of K_c over lines of coarse nodes, two
+                                  block sweeps per application (one cooperative launch); lines
+                                  of at most 640 unknowns (coarse nodes per line x n_eig)     */
+} mstopo_coarse_solver;
+
+typedef enum {
   MSTOPO_FIELD_RHO_TILDE = 0,  /* filtered design (design layout)                         */
   MSTOPO_FIELD_RHO_BAR = 1,    /* projected density of one realisation (design layout)    */
   MSTOPO_FIELD_YOUNG = 2       /* SIMP Young's modulus of one realisation (element layout) */
@@ -74,6 +82,7 @@ typedef struct {
   double local_shift;        /* MIXED only: patch matrices are factorised as K_i + s diag(K_i)
                                 (s >= 0, 0 = exact local solves)                            */
   void* stream;              /* cudaStream_t for all work of this handle, NULL = default   */
+  int32_t coarse_solver;     /* mstopo_coarse_solver for the coarse problem K_c u_c = r_c  */
 } mstopo_problem;
 
 typedef struct {
@@ -83,6 +92,9 @@ typedef struct {
   int32_t eig_sweeps;         /* largest number of subspace-iteration sweeps over all types */
   double eig_residual;        /* largest ||K psi - lambda D psi||_{D^-1} over kept pairs    */
   float ms_hash, ms_eigen, ms_patch_factor, ms_coarse, ms_total;   /* phase times (events)  */
+  int32_t coarse_solver;      /* MSTOPO_COARSE_DENSE or MSTOPO_COARSE_BLOCKTRI, as built   */
+  int32_t coarse_line;        /* unknowns per coarse line (block size of K_c)               */
+  int32_t coarse_lines;       /* number of coarse lines (blocks of K_c)                     */
 } mstopo_build_info;
 
 typedef struct {

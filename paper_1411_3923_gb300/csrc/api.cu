@@ -85,7 +85,8 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             d->nelx / d->H >= 2 && d->nely / d->H >= 2 && d->n_eig >= 1 && d->n_eig <= MSTOPO_MAX_EIG &&
             d->nu >= 0.0 && d->nu < 0.5 && d->Emin > 0.0 && d->Emin <= d->E0 && d->fixed != nullptr &&
             d->tol > 0.0 && d->max_iter > 0 && d->local_shift >= 0.0 &&
-            (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 64;
+            (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 64 &&
+            d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI;
   if (!ok) {
     h->err = "invalid problem description";
     return fail(MSTOPO_INVALID_ARG);
@@ -378,13 +379,13 @@ mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t 
   CKA(cudaMallocAsync(&rm, n * 8, h->s));
   CKA(launch_mask_copy(r, rm, h->d_nmask, h->n_nodes, 1, n, h->s));
   if (precision == MSTOPO_FP64) {
-    CKA(precond_apply_f64(h, rm, z, 1, part));
+    CKA(precond_apply_f64(h, rm, z, 0, 1, part));
   } else {
     float *a, *b;
     CKA(cudaMallocAsync(&a, n * 4, h->s));
     CKA(cudaMallocAsync(&b, n * 4, h->s));
     CKA(launch_convert_d2f(rm, a, n, h->s));
-    CKA(precond_apply_f32(h, a, b, 1, part));
+    CKA(precond_apply_f32(h, a, b, 0, 1, part));
     CKA(launch_convert_f2d(b, z, n, h->s));
     CKA(cudaFreeAsync(a, h->s));
     CKA(cudaFreeAsync(b, h->s));

@@ -129,7 +129,10 @@ struct Precond {
   int* d_grp_type = nullptr;        // [n_groups] patch-solve work items
   int* d_grp_first = nullptr;
   int* d_grp_count = nullptr;
+  int* d_grp_sys = nullptr;         // [n_groups] realisation of the group
+  std::vector<int> h_grp_begin;     // [nsv+1] first group of each realisation
   int n_groups = 0;
+  int nsv = 0;                      // realisations with their own operators
   // per-type patch factors (block tridiagonal by node rows of the (2H+1)^2 agglomerate box,
   // artificial-boundary nodes Dirichlet): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
   uint8_t* d_pfree = nullptr;       // [T][NP*nbP] free DOFs of the patch box
@@ -143,9 +146,15 @@ struct Precond {
   double* d_lambda = nullptr; double* d_psi64 = nullptr; float* d_psi32 = nullptr;
   double* d_eigres = nullptr;       // [T] residual norms
   int* d_eigsweeps = nullptr;       // [T]
-  // coarse problem: dense FP64 inverse of K_c [Nt][Nt]
+  // coarse problem: dense FP64 inverse of K_c [Nt][Nt] (MSTOPO_COARSE_DENSE), or the block
+  // factor over coarse lines (MSTOPO_COARSE_BLOCKTRI): Linv, LinvT, W, V [NLc][nbc][nbc]
+  int coarse_mode = 0, nbc = 0, NLc = 0, sweep_grid = 0;
   double* d_Kc = nullptr;
   double* d_Kcinv = nullptr;
+  double *d_cLinv = nullptr, *d_cLinvT = nullptr, *d_cW = nullptr, *d_cV = nullptr;
+  double *d_cy = nullptr, *d_cx = nullptr;   // [NLc][nbc][4] sweep work vectors
+  int* d_s2o = nullptr;                      // [NLc*nbc] coarse unknown of each line slot
+  unsigned int* d_cbar = nullptr;            // grid-barrier counter of the sweep
   // apply buffers
   double* d_rc = nullptr;           // [MAX_SYS][Nt]
   double* d_uc = nullptr;           // [MAX_SYS][Nt]
@@ -202,13 +211,28 @@ struct mstopo_handle {
   FcgGraph fcg_graph;
 };
 
+// coarse.cu
+cudaError_t coarse_bt_factor(const double* A, const double* B, int nb, int NL, double* Linv,
+                             double* LinvT, double* W, double* V, double* S, double* Cw,
+                             double* Ld, int* status, cudaStream_t s);
+cudaError_t coarse_bt_apply(const double* Linv, const double* LinvT, const double* W,
+                            const double* V, const int* s2o, int nb, int NL, int Nt,
+                            const double* rc, double* uc, int nsys, double* ywork,
+                            double* xwork, unsigned int* bar, int* err, int grid,
+                            cudaStream_t s);
+int coarse_sweep_grid();
+int coarse_sweep_max_nb(int grid, int nsys);
+
 // precond.cu
 mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info);
 void precond_free(Precond& pc);
-// Apply z = M^-1 r for nsys systems (vectors with stride n_dof).  part: 0 both, 1 coarse,
-// 2 patches.  FP32 variant reads/writes float vectors.
-cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int nsys, int part);
-cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int nsys, int part);
+// Apply z = M_k^-1 r for realisations k = sys0 .. sys0+nsys-1 (vectors with stride n_dof,
+// the first one of realisation sys0).  part: 0 both, 1 coarse, 2 patches.  FP32 variant
+// reads/writes float vectors.
+cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int sys0, int nsys,
+                              int part);
+cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sys0, int nsys,
+                              int part);
 
 // krylov.cu
 mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,

@@ -336,11 +336,11 @@ __global__ void k_set_rr(FcgScalars* sc, const double* __restrict__ v, int which
   if (which == 1) c.active = (c.rr > tol2 * c.ff) ? 1 : 0;
 }
 
-static mstopo_status precond(mstopo_handle* h, int nsys) {
+static mstopo_status precond(mstopo_handle* h, int sys0, int nsys) {
   Solver& sv = h->sv;
   cudaError_t e;
-  if (h->p.precision == MSTOPO_FP64) e = precond_apply_f64(h, sv.r, sv.z64, nsys, 0);
-  else e = precond_apply_f32(h, sv.r32, sv.z32, nsys, 0);
+  if (h->p.precision == MSTOPO_FP64) e = precond_apply_f64(h, sv.r, sv.z64, sys0, nsys, 0);
+  else e = precond_apply_f32(h, sv.r32, sv.z32, sys0, nsys, 0);
   CK(e);
   return MSTOPO_OK;
 }
@@ -393,7 +393,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   const double* E64 = h->d_E64 + (long long)sys0 * h->n_el;
   // one flexible-CG iteration for all systems (kernels skip finished systems)
   auto iteration = [&]() -> mstopo_status {
-    mstopo_status s2 = precond(h, nsys);
+    mstopo_status s2 = precond(h, sys0, nsys);
     if (s2 != MSTOPO_OK) return s2;
     if (mixed) CK(launch_dot_partials_f32(sv.z32, sv.q32, n, nsys, n, sv.partials, h->s));
     else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));

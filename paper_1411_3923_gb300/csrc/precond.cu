@@ -57,23 +57,27 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// Hash of the moduli of realisation `salt` over the agglomerate (XOR-accumulated over the
+// realisations, so equal hashes mean equal boxes in every realisation) and, once
+// (with_mask), of its Dirichlet mask.
 __global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restrict__ nmask,
-                           int nelx, int nely, int H, int ncx,
+                           int nelx, int nely, int H, int ncx, int salt, int with_mask,
                            unsigned long long* __restrict__ hash) {
   const int i = blockIdx.x;
   const int I = i % (ncx + 1), J = i / (ncx + 1);
   const int ox = (I - 1) * H, oy = (J - 1) * H;
   const int ne = 2 * H, nn = 2 * H + 1;
+  const unsigned long long sk = mix64(0x5BD1E995ull + (unsigned long long)salt);
   unsigned long long h1 = 0, h2 = 0;
   for (int t = threadIdx.x; t < ne * ne; t += blockDim.x) {
     int ex = ox + t % ne, ey = oy + t / ne;
     unsigned long long v = 0xFFFFFFFFFFFFFFFFull;
     if (ex >= 0 && ex < nelx && ey >= 0 && ey < nely)
       v = (unsigned long long)__double_as_longlong(E[(long long)ey * nelx + ex]);
-    h1 ^= mix64(v ^ mix64((unsigned long long)t * 2 + 1));
-    h2 ^= mix64(v * 0xD6E8FEB86659FD93ull + mix64((unsigned long long)t + 0x1234567ull));
+    h1 ^= mix64(v ^ mix64(((unsigned long long)t * 2 + 1) ^ sk));
+    h2 ^= mix64(v * 0xD6E8FEB86659FD93ull + mix64((unsigned long long)t + 0x1234567ull + sk));
   }
-  for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
+  for (int t = threadIdx.x; with_mask && t < nn * nn; t += blockDim.x) {
     int x = ox + t % nn, y = oy + t / nn;
     unsigned long long v = 7;
     if (x >= 0 && x <= nelx && y >= 0 && y <= nely) v = nmask[(long long)y * (nelx + 1) + x];
@@ -697,22 +701,18 @@ __global__ void __launch_bounds__(PC_THREADS) k_restrict(
   }
 }
 
-// uc[s] = Kcinv rc[s]   (one warp per row, all systems)
+// uc[s] = Kcinv[sys0 + s] rc[s]   (one warp per row; blockIdx.y = system)
 __global__ void k_coarse_gemv(const double* __restrict__ Kinv, const double* __restrict__ rc,
-                              double* __restrict__ uc, int Nt, int nsys) {
+                              double* __restrict__ uc, int Nt, int sys0) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y;
   if (warp >= Nt) return;
-  const double* row = Kinv + (long long)warp * Nt;
-  double acc[MSTOPO_MAX_SYS] = {0, 0, 0, 0};
-  for (int c = lane; c < Nt; c += 32) {
-    const double m = row[c];
-    for (int s = 0; s < nsys; ++s) acc[s] = fma(m, rc[(long long)s * Nt + c], acc[s]);
-  }
-  for (int s = 0; s < nsys; ++s) {
-    double v = acc[s];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) uc[(long long)s * Nt + warp] = v;
-  }
+  const double* row = Kinv + ((long long)(sys0 + s) * Nt + warp) * Nt;
+  const double* v = rc + (long long)s * Nt;
+  double acc = 0.0;
+  for (int c = lane; c < Nt; c += 32) acc = fma(row[c], v[c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) uc[(long long)s * Nt + warp] = acc;
 }
 
 // Patch solves, one CTA per group of up to P patches of one type (all systems: R = 4Q
@@ -744,21 +744,26 @@ __device__ __forceinline__ void load_vec(const T* p, T* v) {
   }
 }
 
+// Groups g0 + blockIdx.x; a group is up to R agglomerates of one type in one realisation
+// (column p = agglomerate p of the group); its right-hand sides come from system
+// grp_sys[g] - sys0 of r.
 template <typename T, int Q, int NBUF>
 __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
-    const T* __restrict__ r, long long stride, int nsys, int nelx, int nely, int H, int ncx,
-    const int* __restrict__ grp_type, const int* __restrict__ grp_first,
-    const int* __restrict__ grp_count, const int* __restrict__ perm,
-    const uint8_t* __restrict__ pfree, const T* __restrict__ fwd, const T* __restrict__ bwd,
-    int nbs, int hrows, T* __restrict__ Xg, int* __restrict__ err) {
+    const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
+    int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
+    const int* __restrict__ grp_first, const int* __restrict__ grp_count,
+    const int* __restrict__ perm, const uint8_t* __restrict__ pfree,
+    const T* __restrict__ fwd, const T* __restrict__ bwd, int nbs, int hrows,
+    T* __restrict__ Xg, int* __restrict__ err) {
   constexpr int R = 4 * Q;
   constexpr int S = PATCH_S;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_abort;
   __shared__ int s_node[PATCH_COLS];   // patch origin per column block: (I-1)H, (J-1)H packed
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int g = blockIdx.x;
+  const int g = g0 + blockIdx.x;
   const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
+  const T* rs = r + (long long)(grp_sys[g] - sys0) * stride;
   const int N = 2 * H + 1, nb = 2 * N, NL = N;
   const long long blk = 2LL * hrows * nbs;
   const uint32_t bytes = (uint32_t)(blk * sizeof(T));
@@ -813,15 +818,14 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
     // input vector of the line
     if (fw) {
       for (int q = threadIdx.x; q < nb * R; q += blockDim.x) {
-        const int c = q / R, col = q % R;
-        const int p = col / nsys, s = col % nsys;
+        const int c = q / R, p = q % R;
         T v = T(0);
-        if (p < cnt && col < cnt * nsys && fr[(long long)k * nb + c]) {
+        if (p < cnt && fr[(long long)k * nb + c]) {
           const int ia = s_node[p];
           const int I = ia % (ncx + 1), J = ia / (ncx + 1);
           const int x = (I - 1) * H + (c >> 1), y = (J - 1) * H + k;
           if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
-            v = r[s * stride + 2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
+            v = rs[2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
         }
         vb[q] = v;
       }
@@ -922,7 +926,7 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
 // One thread per node (2D grid: x fastest), arithmetic in T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_combine(
-    T* __restrict__ z, long long stride, int nsys, int nelx, int nely, int H, int ncx, int ncy,
+    T* __restrict__ z, long long stride, int sys0, int Nc, int nelx, int nely, int H, int ncx, int ncy,
     const int* __restrict__ type_of, const int* __restrict__ kept, const int* __restrict__ coff,
     const T* __restrict__ psi, int kmax, const double* __restrict__ uc, int Nt,
     const int* __restrict__ agg_group, const int* __restrict__ agg_slot, const T* __restrict__ Xg,
@@ -959,8 +963,9 @@ __global__ void __launch_bounds__(256) k_combine(
         zy = fma(chi, ay, zy);
       }
       if (part != 1) {
-        const int col = agg_slot[i] * nsys + s;
-        const long long base = (((long long)agg_group[i] * N + lb) * R + col) * nbP + 2 * la;
+        const long long gi = (long long)(sys0 + s) * Nc + i;
+        const int col = agg_slot[gi];
+        const long long base = (((long long)agg_group[gi] * N + lb) * R + col) * nbP + 2 * la;
         zx += Xg[base];
         zy += Xg[base + 1];
       }
@@ -1040,18 +1045,20 @@ static void dfree(void* p) { if (p) cudaFree(p); }
 
 void precond_free(Precond& pc) {
   dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff); dfree(pc.d_perm);
-  dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count);
+  dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count); dfree(pc.d_grp_sys);
   dfree(pc.d_pfree); dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
   dfree(pc.d_pf64); dfree(pc.d_pb64); dfree(pc.d_pf32); dfree(pc.d_pb32);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
-  dfree(pc.d_Kc); dfree(pc.d_Kcinv); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
+  dfree(pc.d_Kc); dfree(pc.d_Kcinv);
+  dfree(pc.d_cLinv); dfree(pc.d_cLinvT); dfree(pc.d_cW); dfree(pc.d_cV);
+  dfree(pc.d_cy); dfree(pc.d_cx); dfree(pc.d_s2o); dfree(pc.d_cbar); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
   dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
   pc = Precond();
 }
 
 // extra per-agglomerate maps for the combine kernel live behind d_rcpart (ints)
 static int* agg_group_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart); }
-static int* agg_slot_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart) + pc.Nc; }
+static int* agg_slot_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart) + (size_t)pc.nsv * pc.Nc; }
 
 mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) {
   Precond old = h->pc;
@@ -1064,6 +1071,10 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   pc.ncx = h->nelx / H; pc.ncy = h->nely / H; pc.Nc = (pc.ncx + 1) * (pc.ncy + 1);
   pc.kmax = h->p.n_eig;
   pc.local_shift = h->p.precision == MSTOPO_MIXED ? h->p.local_shift : 0.0;
+  // operators per realisation: the coarse basis comes from realisation ref (Sec. 5.3: the
+  // dilated design embeds the others), K_c and the patch matrices from each realisation's
+  // own moduli
+  const int nsv = pc.nsv = h->n_eta;
   const double* E = h->d_E64 + (long long)ref * h->n_el;
   K0P K0;
   for (int q = 0; q < 64; ++q) K0.k[q] = h->K0[q];
@@ -1074,8 +1085,11 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   unsigned long long* d_hash;
   CKB(cudaMalloc(&d_hash, (size_t)pc.Nc * 16));
   CKB(cudaMemsetAsync(d_hash, 0, (size_t)pc.Nc * 16, s));
-  note_launch(), k_hash_agg<<<pc.Nc, PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, H, pc.ncx, d_hash);
-  CKB(cudaGetLastError());
+  for (int k = 0; k < nsv; ++k) {
+    note_launch(), k_hash_agg<<<pc.Nc, PC_THREADS, 0, s>>>(h->d_E64 + (long long)k * h->n_el, h->d_nmask,
+                                                          h->nelx, h->nely, H, pc.ncx, k, k == 0, d_hash);
+    CKB(cudaGetLastError());
+  }
   std::vector<unsigned long long> hh((size_t)pc.Nc * 2);
   CKB(cudaMemcpyAsync(hh.data(), d_hash, (size_t)pc.Nc * 16, cudaMemcpyDeviceToHost, s));
   CKB(cudaStreamSynchronize(s));
@@ -1103,38 +1117,45 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaEventRecord(ev[1], s));
 
   // 2. agglomerate (Neumann, for the eigenproblem) and patch (artificial boundary Dirichlet)
-  //    matrices of every type, both factorised in one launch: systems [0,T) are the shifted
-  //    agglomerate matrices K_w + s diag(K_w), systems [T,2T) the patch matrices
+  //    matrices of every type, all factorised in one launch: systems [0,T) are the shifted
+  //    agglomerate matrices K_w + s diag(K_w) of realisation ref, systems T + k T + t the
+  //    patch matrices of type t in realisation k
   const int NA = pc.NA, nbA = pc.nbA, NP = pc.NP, nbP = pc.nbP;
   const long long nnA = (long long)nbA * nbA, nA = (long long)NA * nbA;
   const long long nnP = nnA, nP = nA;
+  const int TP = T * nsv;             // patch operators
+  const int NS = T + TP;              // factorised systems
   // subspace dimension: 2k + 4 rounded up to a multiple of 4 (compile-time variants)
   const int q = std::min(((2 * pc.kmax + 4) + 3) / 4 * 4, 2 * MSTOPO_MAX_EIG);
   double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY, *dKX, *dYsc, *dGM, *dres;
   uint8_t* dfree_;
   int* d_st;
-  CKB(cudaMalloc(&dA, (size_t)2 * T * NA * nnA * 8));
-  CKB(cudaMalloc(&dB, (size_t)2 * T * (NA - 1) * nnA * 8));
-  CKB(cudaMalloc(&dLi, (size_t)2 * T * NA * nnA * 8));
-  CKB(cudaMalloc(&dC, (size_t)2 * T * (NA - 1) * nnA * 8));
-  CKB(cudaMalloc(&dS, (size_t)2 * T * nnA * 8));
+  CKB(cudaMalloc(&dA, (size_t)NS * NA * nnA * 8));
+  CKB(cudaMalloc(&dB, (size_t)NS * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dLi, (size_t)NS * NA * nnA * 8));
+  CKB(cudaMalloc(&dC, (size_t)NS * (NA - 1) * nnA * 8));
+  CKB(cudaMalloc(&dS, (size_t)NS * nnA * 8));
   CKB(cudaMalloc(&dfree_, (size_t)T * nA));
-  CKB(cudaMalloc(&pc.d_pfree, (size_t)T * nP));
-  CKB(cudaMalloc(&d_st, (size_t)2 * std::max(T, 1) * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_pfree, (size_t)TP * nP));
+  CKB(cudaMalloc(&d_st, (size_t)std::max(NS, 2) * sizeof(int)));
   note_launch(), k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
                                                     pc.ncx, 0, K0, dA, dB, dfree_);
   CKB(cudaGetLastError());
-  note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
-                                                    pc.ncx, 1, K0, dA + (size_t)T * NA * nnA,
-                                                    dB + (size_t)T * (NA - 1) * nnA, pc.d_pfree);
-  CKB(cudaGetLastError());
+  for (int k = 0; k < nsv; ++k) {
+    const size_t o = (size_t)T + (size_t)k * T;
+    note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(h->d_E64 + (long long)k * h->n_el, h->d_nmask,
+                                                      h->nelx, h->nely, d_rep, H, pc.ncx, 1, K0,
+                                                      dA + o * NA * nnA, dB + o * (NA - 1) * nnA,
+                                                      pc.d_pfree + (size_t)k * T * nP);
+    CKB(cudaGetLastError());
+  }
   // the shift flags need a per-system free mask: agglomerate masks, then patch masks
   uint8_t* dfree2;
-  CKB(cudaMalloc(&dfree2, (size_t)2 * T * nA));
+  CKB(cudaMalloc(&dfree2, (size_t)NS * nA));
   CKB(cudaMemcpyAsync(dfree2, dfree_, (size_t)T * nA, cudaMemcpyDeviceToDevice, s));
-  CKB(cudaMemcpyAsync(dfree2 + (size_t)T * nA, pc.d_pfree, (size_t)T * nP, cudaMemcpyDeviceToDevice, s));
-  note_launch(), k_bt_factor<<<2 * T, PC_THREADS, 0, s>>>(dA, dB, dfree2, EIG_SHIFT, pc.local_shift, T, nbA, NA,
-                                                           dLi, dC, dS, d_st);
+  CKB(cudaMemcpyAsync(dfree2 + (size_t)T * nA, pc.d_pfree, (size_t)TP * nP, cudaMemcpyDeviceToDevice, s));
+  note_launch(), k_bt_factor<<<NS, PC_THREADS, 0, s>>>(dA, dB, dfree2, EIG_SHIFT, pc.local_shift, T, nbA, NA,
+                                                       dLi, dC, dS, d_st);
   CKB(cudaGetLastError());
   CKB(cudaMalloc(&dX, (size_t)T * nA * q * 8));
   CKB(cudaMalloc(&dY, (size_t)T * nA * q * 8));
@@ -1168,8 +1189,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     CKB(le);
   }
   CKB(cudaGetLastError());
-  std::vector<int> fst(2 * T);
-  CKB(cudaMemcpyAsync(fst.data(), d_st, 2 * T * sizeof(int), cudaMemcpyDeviceToHost, s));
+  std::vector<int> fst(NS);
+  CKB(cudaMemcpyAsync(fst.data(), d_st, NS * sizeof(int), cudaMemcpyDeviceToHost, s));
   pc.h_kept.resize(T);
   CKB(cudaMemcpyAsync(pc.h_kept.data(), pc.d_kept, T * sizeof(int), cudaMemcpyDeviceToHost, s));
   int werr = 0;
@@ -1184,6 +1205,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       h->err = "agglomerate eigenproblem failed (non-positive pivot or Rayleigh-Ritz breakdown)";
       return MSTOPO_NOT_SPD;
     }
+  }
+  for (int t = 0; t < TP; ++t) {
     if (fst[T + t]) {
       h->err = "patch matrix not positive definite";
       return MSTOPO_NOT_SPD;
@@ -1202,16 +1225,16 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     const double* pLi = dLi + (size_t)T * NA * nnA;
     const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
     double *dW, *dV;
-    CKB(cudaMalloc(&dW, (size_t)T * NP * nnP * 8));
-    CKB(cudaMalloc(&dV, (size_t)T * NP * nnP * 8));
-    note_launch(), k_patch_wv<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
+    CKB(cudaMalloc(&dW, (size_t)TP * NP * nnP * 8));
+    CKB(cudaMalloc(&dV, (size_t)TP * NP * nnP * 8));
+    note_launch(), k_patch_wv<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
     CKB(cudaGetLastError());
-    const size_t pk = (size_t)T * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
+    const size_t pk = (size_t)TP * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
     CKB(cudaMalloc(&pc.d_pf64, pk * 8));
     CKB(cudaMalloc(&pc.d_pb64, pk * 8));
     CKB(cudaMalloc(&pc.d_pf32, pk * 4));
     CKB(cudaMalloc(&pc.d_pb32, pk * 4));
-    note_launch(), k_patch_pack<<<dim3(T, NP, 2), PC_THREADS, 0, s>>>(pLi, dW, dV, nbP, NP, pc.rpc,
+    note_launch(), k_patch_pack<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, dW, dV, nbP, NP, pc.rpc,
                                                                     pc.nbs, pc.d_pf64, pc.d_pb64,
                                                                     pc.d_pf32, pc.d_pb32);
     CKB(cudaGetLastError());
@@ -1247,73 +1270,137 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       for (int a = 0; a < k; ++a) slot2orig[(size_t)L * nbc + P * pc.kmax + a] = pc.h_coff[i] + a;
     }
   int* d_s2o;
-  double *cA, *cB, *cLi, *cC, *cS, *cX;
+  double *cA, *cB, *cLi, *cC, *cS, *cX = nullptr;
+  const size_t nlA = (size_t)NLc * nnc, nlB = (size_t)std::max(NLc - 1, 1) * nnc;
   CKB(cudaMalloc(&d_s2o, slot2orig.size() * sizeof(int)));
   CKB(cudaMemcpyAsync(d_s2o, slot2orig.data(), slot2orig.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMalloc(&cA, (size_t)NLc * nnc * 8));
-  CKB(cudaMalloc(&cB, (size_t)std::max(NLc - 1, 1) * nnc * 8));
-  CKB(cudaMalloc(&cLi, (size_t)NLc * nnc * 8));
-  CKB(cudaMalloc(&cC, (size_t)std::max(NLc - 1, 1) * nnc * 8));
-  CKB(cudaMalloc(&cS, (size_t)nnc * 8));
-  CKB(cudaMemsetAsync(cA, 0, (size_t)NLc * nnc * 8, s));
-  CKB(cudaMemsetAsync(cB, 0, (size_t)std::max(NLc - 1, 1) * nnc * 8, s));
-  note_launch(), k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(E, h->nelx, h->nely, H, pc.d_type_of_agg,
-                                                          pc.d_kept, pc.d_psi64, pc.kmax, K0, cm,
-                                                          cA, cB, nbc);
-  CKB(cudaGetLastError());
-  // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
-  note_launch(), k_bt_factor<<<1, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, 0.0, 1, nbc, NLc, cLi, cC, cS, d_st);
-  CKB(cudaGetLastError());
-  int cst = 0;
-  CKB(cudaMemcpyAsync(&cst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CKB(cudaMalloc(&pc.d_Kcinv, (size_t)Nt * Nt * 8));
-  const int nblk = cdiv((long long)NLc * nbc, RC);
-  CKB(cudaMalloc(&cX, (size_t)nblk * NLc * nbc * RC * 8));
-  CKB(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nbc * RC * 8));
-  note_launch(), k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi, cC, nbc, NLc, d_s2o, Nt, cX, pc.d_Kcinv);
-  CKB(cudaGetLastError());
-  CKB(cudaStreamSynchronize(s));
-  cudaFree(cA); cudaFree(cB); cudaFree(cLi); cudaFree(cC); cudaFree(cS); cudaFree(cX); cudaFree(d_s2o);
-  if (cst) {
-    h->err = "coarse matrix K_c not positive definite";
-    return MSTOPO_NOT_SPD;
+  CKB(cudaMalloc(&cA, nsv * nlA * 8));
+  CKB(cudaMalloc(&cB, nsv * nlB * 8));
+  CKB(cudaMemsetAsync(cA, 0, nsv * nlA * 8, s));
+  CKB(cudaMemsetAsync(cB, 0, nsv * nlB * 8, s));
+  for (int k = 0; k < nsv; ++k) {   // K_c of realisation k on the shared basis
+    note_launch(), k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(h->d_E64 + (long long)k * h->n_el,
+                                                            h->nelx, h->nely, H, pc.d_type_of_agg,
+                                                            pc.d_kept, pc.d_psi64, pc.kmax, K0, cm,
+                                                            cA + k * nlA, cB + k * nlB, nbc);
+    CKB(cudaGetLastError());
   }
+  // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
+  int mode = h->p.coarse_solver;
+  if (mode == MSTOPO_COARSE_AUTO) mode = Nt <= 4096 ? MSTOPO_COARSE_DENSE : MSTOPO_COARSE_BLOCKTRI;
+  pc.coarse_mode = mode;
+  pc.nbc = nbc;
+  pc.NLc = NLc;
+  std::vector<int> cst(nsv, 0);
+  CKB(cudaMemsetAsync(d_st, 0, nsv * sizeof(int), s));
+  if (mode == MSTOPO_COARSE_DENSE) {
+    // one-CTA block factor per realisation, then the explicit inverses by identity columns
+    CKB(cudaMalloc(&cLi, nsv * nlA * 8));
+    CKB(cudaMalloc(&cC, nsv * nlB * 8));
+    CKB(cudaMalloc(&cS, nsv * nnc * 8));
+    note_launch(), k_bt_factor<<<nsv, PC_THREADS, 0, s>>>(cA, cB, nullptr, 0.0, 0.0, nsv, nbc, NLc, cLi, cC, cS, d_st);
+    CKB(cudaGetLastError());
+    CKB(cudaMalloc(&pc.d_Kcinv, (size_t)nsv * Nt * Nt * 8));
+    const int nblk = cdiv((long long)NLc * nbc, RC);
+    CKB(cudaMalloc(&cX, (size_t)nblk * NLc * nbc * RC * 8));
+    CKB(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nbc * RC * 8));
+    for (int k = 0; k < nsv; ++k) {
+      note_launch(), k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi + k * nlA, cC + k * nlB, nbc, NLc, d_s2o, Nt, cX,
+                                                                                 pc.d_Kcinv + (size_t)k * Nt * Nt);
+      CKB(cudaGetLastError());
+    }
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(cX); cudaFree(cLi); cudaFree(cC); cudaFree(cS);
+    cudaFree(d_s2o);
+  } else {
+    // block factor with whole-GPU dense kernels per realisation, applied by cooperative sweeps
+    pc.sweep_grid = coarse_sweep_grid();
+    if (pc.sweep_grid <= 0 || nbc > coarse_sweep_max_nb(pc.sweep_grid, nsv)) {
+      cudaFree(cA); cudaFree(cB); cudaFree(d_s2o);
+      h->err = "coarse line too long for the block-tridiagonal coarse solver (coarse nodes per line x n_eig "
+               "x realisations > 2432, or coarse nodes per line x n_eig > 640)";
+      return MSTOPO_INVALID_ARG;
+    }
+    double* cLd;
+    CKB(cudaMalloc(&pc.d_cLinv, nsv * nlA * 8));
+    CKB(cudaMalloc(&pc.d_cLinvT, nsv * nlA * 8));
+    CKB(cudaMalloc(&pc.d_cW, nsv * nlA * 8));
+    CKB(cudaMalloc(&pc.d_cV, nsv * nlA * 8));
+    CKB(cudaMalloc(&cLd, (size_t)cdiv(nbc, 32) * 32 * 32 * 8));
+    CKB(cudaMalloc(&cC, (size_t)2 * nnc * 8));
+    CKB(cudaMalloc(&cS, (size_t)nnc * 8));
+    for (int k = 0; k < nsv; ++k)
+      CKB(coarse_bt_factor(cA + k * nlA, cB + k * nlB, nbc, NLc, pc.d_cLinv + k * nlA,
+                           pc.d_cLinvT + k * nlA, pc.d_cW + k * nlA, pc.d_cV + k * nlA, cS, cC, cLd,
+                           d_st + k, s));
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(cLd); cudaFree(cC); cudaFree(cS);
+    pc.d_s2o = d_s2o;
+    CKB(cudaMalloc(&pc.d_cy, (size_t)MSTOPO_MAX_SYS * NLc * nbc * 8));
+    CKB(cudaMalloc(&pc.d_cx, (size_t)MSTOPO_MAX_SYS * NLc * nbc * 8));
+    CKB(cudaMalloc(&pc.d_cbar, sizeof(unsigned int)));
+  }
+  CKB(cudaMemcpy(cst.data(), d_st, nsv * sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(cA); cudaFree(cB);
+  for (int k = 0; k < nsv; ++k)
+    if (cst[k]) {
+      h->err = "coarse matrix K_c not positive definite";
+      return MSTOPO_NOT_SPD;
+    }
   CKB(cudaEventRecord(ev[4], s));
 
-  // 5. patch-solve work groups (per type, PC_GROUP agglomerates each) and apply buffers
+  // 5. patch-solve work groups: per realisation k and type t, P agglomerates each (one
+  //    right-hand-side column per agglomerate); groups of realisation k are
+  //    [grp_begin[k], grp_begin[k+1]).  P grows with the work so that about one CTA per SM
+  //    runs on small meshes and the block streaming is shared by up to PATCH_COLS columns
+  //    on large ones.
   std::vector<std::vector<int>> by_type(T);
   for (int i = 0; i < pc.Nc; ++i) by_type[pc.h_type_of_agg[i]].push_back(i);
-  std::vector<int> perm, gt, gf, gc, agg_group(pc.Nc), agg_slot(pc.Nc);
-  // four patches per CTA keeps ~one CTA per SM at the 1024x512 size; more columns per CTA
-  // would amortise the block streaming further but leave SMs idle
-  const int P = std::max(1, std::min(PATCH_GROUP, PATCH_COLS / std::max(1, h->n_eta)));
+  std::vector<int> perm, gt, gf, gc, gs, agg_group((size_t)nsv * pc.Nc), agg_slot((size_t)nsv * pc.Nc);
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int P = std::max(1, std::min(PATCH_COLS, (pc.Nc * nsv + sms - 1) / std::max(sms, 1)));
   pc.patches_per_group = P;
-  for (int t = 0; t < T; ++t)
-    for (size_t b = 0; b < by_type[t].size(); b += P) {
-      int g = (int)gt.size();
-      gt.push_back(t);
-      gf.push_back((int)perm.size());
-      int c = (int)std::min<size_t>(P, by_type[t].size() - b);
-      gc.push_back(c);
-      for (int p = 0; p < c; ++p) {
-        int i = by_type[t][b + p];
-        agg_group[i] = g;
-        agg_slot[i] = p;
-        perm.push_back(i);
+  pc.h_grp_begin.assign(nsv + 1, 0);
+  for (int k = 0; k < nsv; ++k) {
+    pc.h_grp_begin[k] = (int)gt.size();
+    for (int t = 0; t < T; ++t)
+      for (size_t b = 0; b < by_type[t].size(); b += P) {
+        int g = (int)gt.size();
+        gt.push_back(k * T + t);
+        gs.push_back(k);
+        gf.push_back((int)perm.size());
+        int c = (int)std::min<size_t>(P, by_type[t].size() - b);
+        gc.push_back(c);
+        for (int p = 0; p < c; ++p) {
+          int i = by_type[t][b + p];
+          agg_group[(size_t)k * pc.Nc + i] = g;
+          agg_slot[(size_t)k * pc.Nc + i] = p;
+          perm.push_back(i);
+        }
       }
-    }
+  }
+  pc.h_grp_begin[nsv] = (int)gt.size();
   pc.n_groups = (int)gt.size();
   CKB(cudaMalloc(&pc.d_perm, perm.size() * sizeof(int)));
   CKB(cudaMalloc(&pc.d_grp_type, gt.size() * sizeof(int)));
   CKB(cudaMalloc(&pc.d_grp_first, gf.size() * sizeof(int)));
   CKB(cudaMalloc(&pc.d_grp_count, gc.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_rcpart, (size_t)2 * pc.Nc * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_grp_sys, gs.size() * sizeof(int)));
+  CKB(cudaMalloc(&pc.d_rcpart, (size_t)2 * nsv * pc.Nc * sizeof(int)));
   CKB(cudaMemcpyAsync(pc.d_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaMemcpyAsync(pc.d_grp_type, gt.data(), gt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaMemcpyAsync(pc.d_grp_first, gf.data(), gf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaMemcpyAsync(pc.d_grp_count, gc.data(), gc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(agg_group_ptr(pc), agg_group.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(agg_slot_ptr(pc), agg_slot.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(pc.d_grp_sys, gs.data(), gs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(agg_group_ptr(pc), agg_group.data(), agg_group.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMemcpyAsync(agg_slot_ptr(pc), agg_slot.data(), agg_slot.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  // the host copies above read vectors that go out of scope: wait for them
+  CKB(cudaStreamSynchronize(s));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   const size_t xg = (size_t)pc.n_groups * nP * PATCH_COLS;
@@ -1330,6 +1417,9 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     info->n_agglomerates = pc.Nc;
     info->n_types = T;
     info->n_coarse = Nt;
+    info->coarse_solver = pc.coarse_mode;
+    info->coarse_line = pc.nbc;
+    info->coarse_lines = pc.NLc;
     info->eig_sweeps = *std::max_element(esw.begin(), esw.end());
     info->eig_residual = *std::max_element(eres.begin(), eres.end());
     cudaEventElapsedTime(&info->ms_hash, ev[0], ev[1]);
@@ -1344,8 +1434,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
 }
 
 template <typename T, int Q>
-static cudaError_t launch_patch(mstopo_handle* h, const T* r, int nsys, const T* fwd, const T* bwd,
-                                T* Xg) {
+static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys, const T* fwd,
+                                const T* bwd, T* Xg) {
   Precond& pc = h->pc;
   const int nb = pc.nbP, R = 4 * Q;
   constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
@@ -1361,14 +1451,16 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int nsys, const T*
     attr_set = true;
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
-  note_launch(), k_patch_solve_f<T, Q, NBUF><<<pc.n_groups, PATCH_THREADS, sm, h->s>>>(
-      r, h->n_dof, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_first,
-      pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg, h->d_flag + 1);
+  const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;
+  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, PATCH_THREADS, sm, h->s>>>(
+      r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_sys,
+      pc.d_grp_first, pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
+      h->d_flag + 1);
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int part,
+static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int nsys, int part,
                               const T* psi, const T* fwd, const T* bwd, T* Xg) {
   Precond& pc = h->pc;
   cudaStream_t s = h->s;
@@ -1378,37 +1470,47 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int nsys, int 
                                                           pc.d_type_of_agg, pc.d_kept, pc.d_coff,
                                                           psi, pc.kmax, pc.d_rc, pc.Nt);
     cudaEvent_t pa = prof_begin(h->prof, s);
-    note_launch(), k_coarse_gemv<<<cdiv((long long)pc.Nt * 32, 256), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, nsys);
+    if (pc.coarse_mode == MSTOPO_COARSE_BLOCKTRI) {
+      const long long so = (long long)sys0 * pc.NLc * pc.nbc * pc.nbc;
+      cudaError_t e = coarse_bt_apply(pc.d_cLinv + so, pc.d_cLinvT + so, pc.d_cW + so, pc.d_cV + so,
+                                      pc.d_s2o, pc.nbc, pc.NLc, pc.Nt, pc.d_rc, pc.d_uc, nsys,
+                                      pc.d_cy, pc.d_cx, pc.d_cbar, h->d_flag + 1, pc.sweep_grid, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      note_launch(), k_coarse_gemv<<<dim3(cdiv((long long)pc.Nt * 32, 256), nsys), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, sys0);
+    }
     prof_end(h->prof, PROF_COARSE, pa, s);
   }
   int Rcols = 4;
   if (part != 1) {
-    const int Q = (pc.patches_per_group * nsys + 3) / 4;
+    const int Q = (pc.patches_per_group + 3) / 4;
     Rcols = 4 * Q;
     cudaEvent_t pa = prof_begin(h->prof, s);
     cudaError_t e;
     switch (Q) {
-      case 1: e = launch_patch<T, 1>(h, r, nsys, fwd, bwd, Xg); break;
-      case 2: e = launch_patch<T, 2>(h, r, nsys, fwd, bwd, Xg); break;
-      case 3: e = launch_patch<T, 3>(h, r, nsys, fwd, bwd, Xg); break;
-      default: e = launch_patch<T, 4>(h, r, nsys, fwd, bwd, Xg); break;
+      case 1: e = launch_patch<T, 1>(h, r, sys0, nsys, fwd, bwd, Xg); break;
+      case 2: e = launch_patch<T, 2>(h, r, sys0, nsys, fwd, bwd, Xg); break;
+      case 3: e = launch_patch<T, 3>(h, r, sys0, nsys, fwd, bwd, Xg); break;
+      default: e = launch_patch<T, 4>(h, r, sys0, nsys, fwd, bwd, Xg); break;
     }
     if (e != cudaSuccess) return e;
     prof_end(h->prof, PROF_PATCH, pa, s);
   }
-  note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, nsys, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
+  note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, sys0, pc.Nc, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
                                                pc.d_uc, pc.Nt, agg_group_ptr(pc), agg_slot_ptr(pc), Xg,
                                                Rcols, h->d_nmask, part);
   return cudaGetLastError();
 }
 
-cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int nsys, int part) {
+cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int sys0, int nsys,
+                              int part) {
   Precond& pc = h->pc;
-  return apply_impl<double>(h, r, z, nsys, part, pc.d_psi64, pc.d_pf64, pc.d_pb64, pc.d_zp64);
+  return apply_impl<double>(h, r, z, sys0, nsys, part, pc.d_psi64, pc.d_pf64, pc.d_pb64, pc.d_zp64);
 }
 
-cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int nsys, int part) {
+cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sys0, int nsys,
+                              int part) {
   Precond& pc = h->pc;
-  return apply_impl<float>(h, r, z, nsys, part, pc.d_psi32, pc.d_pf32, pc.d_pb32, pc.d_zp32);
+  return apply_impl<float>(h, r, z, sys0, nsys, part, pc.d_psi32, pc.d_pf32, pc.d_pb32, pc.d_zp32);
 }

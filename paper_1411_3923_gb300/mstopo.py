@@ -33,20 +33,24 @@ class _Problem(C.Structure):
                 ("Emin", C.c_double), ("penal", C.c_double), ("fixed", C.c_void_p),
                 ("H", C.c_int32), ("n_eig", C.c_int32), ("lambda_thresh", C.c_double),
                 ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("local_shift", C.c_double), ("stream", C.c_void_p)]
+                ("local_shift", C.c_double), ("stream", C.c_void_p),
+                ("coarse_solver", C.c_int32)]
 
 
 class _BuildInfo(C.Structure):
     _fields_ = [("n_agglomerates", C.c_int32), ("n_types", C.c_int32), ("n_coarse", C.c_int32),
                 ("eig_sweeps", C.c_int32), ("eig_residual", C.c_double), ("ms_hash", C.c_float),
                 ("ms_eigen", C.c_float), ("ms_patch_factor", C.c_float), ("ms_coarse", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("coarse_solver", C.c_int32),
+                ("coarse_line", C.c_int32), ("coarse_lines", C.c_int32)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("kernel_launches", C.c_int64 * 4),
                 ("kernel_ms", C.c_double * 4)]
 
+
+COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
 
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
 
@@ -127,14 +131,14 @@ class Problem:
                  E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
                  n_eig: int = 4, lambda_thresh: float = 0.0, precision: str = "mixed",
                  tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, coarse_solver: str = "auto"):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
         assert self._fixed.size == 2 * (nelx + 1) * (nely + 1)
         d = _Problem(nelx, nely, nu, E0, Emin, penal, self._fixed.ctypes.data, H, n_eig,
                      lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
-                     local_shift, stream)
+                     local_shift, stream, COARSE_SOLVERS[coarse_solver])
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:

@@ -105,13 +105,22 @@ def jittered_void_tiling(nelx: int, nely: int, cell: int, radius: float, rng) ->
     return rho
 
 
-def layered(nelx: int, nely: int, rng, tmin: int = 4, tmax: int = 12) -> np.ndarray:
-    """Horizontal layers, alternately solid and void from the bottom, thickness U{tmin..tmax}."""
+def layered(nelx: int, nely: int, rng, tmin: int = 4, tmax: int = 12, period: int = 32,
+            strut: int = 8) -> np.ndarray:
+    """Horizontal layers, alternately solid and void from the bottom, thickness U{tmin..tmax}.
+    Every void layer is crossed by solid struts ``strut`` elements wide, one per ``period``
+    elements along x, at a seeded offset per layer, so that the stiff layers form one
+    connected structure (without them each stiff layer floats on the void material)."""
     rho = np.empty((nely, nelx))
+    x = np.arange(nelx)
     y, solid = 0, True
     while y < nely:
         t = int(rng.integers(tmin, tmax + 1))
-        rho[y:y + t, :] = 1.0 if solid else 0.0
+        if solid:
+            rho[y:y + t, :] = 1.0
+        else:
+            off = int(rng.integers(0, period))
+            rho[y:y + t, :] = np.where((x - off) % period < strut, 1.0, 0.0)[None, :]
         y += t
         solid = not solid
     return rho
