@@ -551,8 +551,10 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
     const double* __restrict__ E, int nelx, int nely, int H, const int* __restrict__ type_of,
     const int* __restrict__ kept, const double* __restrict__ psi, int kmax, K0P K0, CoarseMap cm,
     double* __restrict__ Ac, double* __restrict__ Bc, int nbc) {
-  // blockIdx.x = agglomerate i, blockIdx.y = neighbour (dI, dJ) in [-1,1]^2
-  __shared__ double red[PC_THREADS / MSTOPO_MAX_EIG][MSTOPO_MAX_EIG][MSTOPO_MAX_EIG + 1];
+  // blockIdx.x = agglomerate i, blockIdx.y = neighbour (dI, dJ) in [-1,1]^2.
+  // Thread = (element lane, column b of agglomerate 2); kp columns per lane (kmax rounded up
+  // to 4, 8 or 16), 256 / kp element lanes.
+  __shared__ double red[PC_THREADS][MSTOPO_MAX_EIG + 1];
   const int ncx = cm.ncx, ncy = cm.ncy;
   const int i = blockIdx.x;
   const int I = i % (ncx + 1), J = i / (ncx + 1);
@@ -572,8 +574,10 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
   // element overlap of the two agglomerates, inside the mesh
   const int x0 = max(max((I - 1) * H, (I2 - 1) * H), 0), x1 = min(min((I + 1) * H, (I2 + 1) * H), nelx);
   const int y0 = max(max((J - 1) * H, (J2 - 1) * H), 0), y1 = min(min((J + 1) * H, (J2 + 1) * H), nely);
-  const int lanes = PC_THREADS / MSTOPO_MAX_EIG;     // element lanes
-  const int b = threadIdx.x % MSTOPO_MAX_EIG, lane = threadIdx.x / MSTOPO_MAX_EIG;
+  const int kp = kmax <= 4 ? 4 : (kmax <= 8 ? 8 : 16);
+  const int lanes = PC_THREADS / kp;
+  const int b = threadIdx.x % kp, lane = threadIdx.x / kp;
+  const double invH2 = 1.0 / (double)(H * H);
   double acc[MSTOPO_MAX_EIG];
   for (int a = 0; a < MSTOPO_MAX_EIG; ++a) acc[a] = 0.0;
   const int nex = x1 - x0, ney = y1 - y0;
@@ -587,8 +591,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
 #pragma unroll
       for (int ln = 0; ln < 4; ++ln) {
         const int nx = ex + ((ln == 1 || ln == 2) ? 1 : 0), ny = ey + (ln >= 2 ? 1 : 0);
-        c1[ln] = hat(nx, I * H, H) * hat(ny, J * H, H);
-        const double c2 = hat(nx, I2 * H, H) * hat(ny, J2 * H, H);
+        // bilinear hats with integer numerators (H - |x - IH|)(H - |y - JH|) / H^2
+        const int h1x = max(H - abs(nx - I * H), 0), h1y = max(H - abs(ny - J * H), 0);
+        const int h2x = max(H - abs(nx - I2 * H), 0), h2y = max(H - abs(ny - J2 * H), 0);
+        c1[ln] = (double)(h1x * h1y) * invH2;
+        const double c2 = (double)(h2x * h2y) * invH2;
         l1[ln] = (long long)(ny - (J - 1) * H) * N + (nx - (I - 1) * H);
         const long long l2 = (long long)(ny - (J2 - 1) * H) * N + (nx - (I2 - 1) * H);
         f2[2 * ln] = c2 * P2s[(l2 * 2) * kmax + b];
@@ -596,16 +603,19 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
       }
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
+        if (c1[rr >> 1] == 0.0) continue;
         double sdot = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) sdot = fma(K0.k[rr * 8 + c], f2[c], sdot);
         const double w = Ee * sdot * c1[rr >> 1];
         const double* p1 = P1s + (l1[rr >> 1] * 2 + (rr & 1)) * kmax;
-        for (int a = 0; a < k1; ++a) acc[a] = fma(w, p1[a], acc[a]);
+#pragma unroll
+        for (int a = 0; a < MSTOPO_MAX_EIG; ++a)
+          if (a < k1) acc[a] = fma(w, p1[a], acc[a]);
       }
     }
   }
-  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) red[lane][b][a] = acc[a];
+  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) red[threadIdx.x][a] = acc[a];
   __syncthreads();
   // reduce over lanes in fixed order and write the block
   const int nn = nbc;
@@ -613,7 +623,8 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
     const int bb = t / MSTOPO_MAX_EIG, aa = t % MSTOPO_MAX_EIG;
     if (aa >= kmax || bb >= kmax) continue;
     double s = 0.0;
-    for (int l = 0; l < lanes; ++l) s += red[l][bb][aa];
+    if (bb < kp)
+      for (int l = 0; l < lanes; ++l) s += red[l * kp + bb][aa];
     const int row_slot = P1 * kmax + aa, col_slot = P2 * kmax + bb;
     double v;
     if (aa < k1 && bb < k2) v = s;
@@ -746,9 +757,21 @@ __device__ __forceinline__ void load_vec(const T* p, T* v) {
 
 // Groups g0 + blockIdx.x; a group is up to R agglomerates of one type in one realisation
 // (column p = agglomerate p of the group); its right-hand sides come from system
-// grp_sys[g] - sys0 of r.
+// grp_sys[g] - sys0 of r.  The R columns are split over patch_cg(Q) thread groups of
+// PATCH_THREADS threads (patch_cpt(Q) columns each), which multiplies the warps that hide
+// the shared-memory latency of the row products.
+__host__ __device__ constexpr int patch_cpt(int Q) { return Q == 4 ? 8 : 4; }
+__host__ __device__ constexpr int patch_cg(int Q) { return 4 * Q / patch_cpt(Q); }
+// Row stride of the right-hand-side vectors in shared memory: the 8 lanes that share a row
+// pair read 8 consecutive rows with 16-byte loads, which are bank-conflict free when a row
+// is an odd number of 16-byte chunks.
+template <typename T>
+__host__ __device__ constexpr int patch_rs(int R) {
+  return sizeof(T) == 4 ? ((R / 4) % 2 == 0 ? R + 4 : R) : R + 2;
+}
+
 template <typename T, int Q, int NBUF>
-__global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
+__global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
     const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
     int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
     const int* __restrict__ grp_first, const int* __restrict__ grp_count,
@@ -756,6 +779,7 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
     const T* __restrict__ fwd, const T* __restrict__ bwd, int nbs, int hrows,
     T* __restrict__ Xg, int* __restrict__ err) {
   constexpr int R = 4 * Q;
+  constexpr int RS = patch_rs<T>(R);
   constexpr int S = PATCH_S;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_abort;
@@ -768,9 +792,9 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
   const long long blk = 2LL * hrows * nbs;
   const uint32_t bytes = (uint32_t)(blk * sizeof(T));
   T* stg = reinterpret_cast<T*>(smraw);                 // [NBUF][2][hrows][nbs]
-  T* vb = stg + NBUF * blk;                             // [nbs][R] input b_k or y_k
-  T* prev = vb + (long long)nbs * R;                    // [nbs][R] y_{k-1} or x_{k+1}
-  T* cur = prev + (long long)nbs * R;                   // [nbs][R] this line's result
+  T* vb = stg + NBUF * blk;                             // [nbs][RS] input b_k or y_k
+  T* prev = vb + (long long)nbs * RS;                   // [nbs][RS] y_{k-1} or x_{k+1}
+  T* cur = prev + (long long)nbs * RS;                  // [nbs][RS] this line's result
   const uint8_t* fr = pfree + (long long)type * N * nb;
   T* X = Xg + (long long)g * NL * R * nb;
   if (threadIdx.x < PATCH_COLS) {
@@ -800,12 +824,15 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
       bulk_g2s(stg + b * blk, src(b), bytes, &bars[b]);
     }
   uint32_t phase[2] = {0u, 0u};
-  // thread roles: a pair of rows (rl, rl + hp) of the half block, reduction part pp of S
-  const int t = threadIdx.x;
+  // thread roles: column group cgi (columns j0 .. j0 + CPT), a pair of rows (rl, rl + hp)
+  // of the half block, reduction part pp of S
+  constexpr int CPT = patch_cpt(Q);
+  const int cgi = threadIdx.x / PATCH_THREADS, t = threadIdx.x % PATCH_THREADS;
+  const int j0 = cgi * CPT;
   const int pp = t % S, rl = t / S;
   const int hp = (hrows + 1) >> 1;
   // zero the padding rows of the vectors once (nb..nbs-1) so the inner loops need no bounds
-  for (int q = nb * R + threadIdx.x; q < nbs * R; q += blockDim.x) {
+  for (int q = nb * RS + threadIdx.x; q < nbs * RS; q += blockDim.x) {
     vb[q] = T(0);
     prev[q] = T(0);
     cur[q] = T(0);
@@ -827,11 +854,11 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
           if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
             v = rs[2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
         }
-        vb[q] = v;
+        vb[c * RS + p] = v;
       }
     } else {
       const T* yk = X + (long long)k * nb * R;
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[q] = yk[q];
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[(q / R) * RS + q % R] = yk[q];
     }
     __syncthreads();
     for (int half = 0; half < 2; ++half, ++m) {
@@ -848,9 +875,9 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
       const bool va = ra < hp && half * hrows + ra < nb;
       const bool vbr = va && rb < hrows && half * hrows + rb < nb;
       const int ia = half * hrows + ra, ib = half * hrows + rb;
-      T acc0[R], acc1[R];
+      T acc0[CPT], acc1[CPT];
 #pragma unroll
-      for (int j = 0; j < R; ++j) { acc0[j] = T(0); acc1[j] = T(0); }
+      for (int j = 0; j < CPT; ++j) { acc0[j] = T(0); acc1[j] = T(0); }
       if (va) {
         // lanes of a row pair take every S-th column (conflict-free shared loads of both the
         // matrix rows and the vectors); the factor is zero outside each row's triangle
@@ -861,10 +888,10 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
 #pragma unroll 4
         for (int c = c0 + pp; c < c1; c += S) {
           const T a0 = Ar0[c], a1 = Ar1[c];
-          T v[R];
-          load_vec<T, R>(vb + c * R, v);
+          T v[CPT];
+          load_vec<T, CPT>(vb + c * RS + j0, v);
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
+          for (int j = 0; j < CPT; ++j) {
             acc0[j] = fma(a0, v[j], acc0[j]);
             acc1[j] = fma(a1, v[j], acc1[j]);
           }
@@ -875,10 +902,10 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
 #pragma unroll 4
           for (int c = pp; c < nb; c += S) {
             const T a0 = Br0[c], a1 = Br1[c];
-            T v[R];
-            load_vec<T, R>(prev + c * R, v);
+            T v[CPT];
+            load_vec<T, CPT>(prev + c * RS + j0, v);
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
+            for (int j = 0; j < CPT; ++j) {
               acc0[j] = fma(-a0, v[j], acc0[j]);
               acc1[j] = fma(-a1, v[j], acc1[j]);
             }
@@ -888,18 +915,18 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
 #pragma unroll
       for (int o = 1; o < S; o <<= 1)
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < CPT; ++j) {
           acc0[j] += __shfl_xor_sync(0xffffffffu, acc0[j], o);
           acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], o);
         }
       if (pp == 0) {
         if (va) {
 #pragma unroll
-          for (int j = 0; j < R; ++j) cur[ia * R + j] = acc0[j];
+          for (int j = 0; j < CPT; ++j) cur[ia * RS + j0 + j] = acc0[j];
         }
         if (vbr) {
 #pragma unroll
-          for (int j = 0; j < R; ++j) cur[ib * R + j] = acc1[j];
+          for (int j = 0; j < CPT; ++j) cur[ib * RS + j0 + j] = acc1[j];
         }
       }
       __syncthreads();   // block b consumed: refill it
@@ -911,9 +938,9 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve_f(
     // publish the line: forward y_k -> work buffer [nb][R]; backward x_k -> [R][nb]
     T* Xk = X + (long long)k * nb * R;
     if (fw) {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[q];
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q / R) * RS + q % R];
     } else {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q % nb) * R + q / nb];
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q % nb) * RS + q / nb];
     }
     // the result becomes the previous-line vector
     T* tmp = prev; prev = cur; cur = tmp;
@@ -1220,7 +1247,10 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
 
   // 3. patch factors: W_k, V_k and the packed stage blocks (FP64 and FP32)
   pc.rpc = (nbP + PATCH_HALVES - 1) / PATCH_HALVES;
+  // factor row stride: a multiple of 4 with stride = 8 (mod 32) floats, so that the four row
+  // pairs a warp reads in one shared load fall on disjoint banks
   pc.nbs = (nbP + 3) / 4 * 4;
+  while (pc.nbs % 32 != 8) pc.nbs += 4;
   {
     const double* pLi = dLi + (size_t)T * NA * nnA;
     const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
@@ -1440,7 +1470,7 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
   const int nb = pc.nbP, R = 4 * Q;
   constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
   const long long blk = 2LL * pc.rpc * pc.nbs;
-  const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * R) * sizeof(T);
+  const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * patch_rs<T>(R)) * sizeof(T);
   (void)nb;
   // the shared-memory limit is raised once per instantiation (never inside a graph capture)
   static bool attr_set = false;
@@ -1452,7 +1482,7 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
   const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;
-  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, PATCH_THREADS, sm, h->s>>>(
+  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, PATCH_THREADS * patch_cg(Q), sm, h->s>>>(
       r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_sys,
       pc.d_grp_first, pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
       h->d_flag + 1);
