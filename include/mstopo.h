@@ -151,6 +151,22 @@ mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* 
 mstopo_status mstopo_solve_host(mstopo_handle* h, int32_t realisation, const double* f,
                                 double* u, const double* u0, mstopo_solve_info* infos);
 
+/* Batches of independent instances (for example meshes of uneven sizes): the instances'
+ * calls run concurrently, each on its own handle and stream from its own host
+ * thread (at most 16 threads), so their kernels overlap on the GPU.  Handles must be
+ * distinct and should not share a stream (a shared stream serialises them).
+ * mstopo_batch_build_preconditioner: as mstopo_build_preconditioner(hs[b], ref, infos + b)
+ *   for every b; infos: HOST array of n, may be NULL.
+ * mstopo_batch_solve: as mstopo_solve(hs[b], -1, f[b], u[b], NULL, infos + 4 b) for every
+ *   b (all realisations of every instance); f, u: HOST arrays of n DEVICE pointers;
+ *   infos: HOST array of 4 n (instance b's realisations at 4 b), may be NULL.
+ * Both return OK, or the status of the first instance (in batch order) that failed; the
+ * other instances still complete.  Errors: INVALID_ARG (NULL or repeated handle, n < 1). */
+mstopo_status mstopo_batch_build_preconditioner(mstopo_handle* const* hs, int32_t n, int32_t ref,
+                                                mstopo_build_info* infos);
+mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const double* const* f,
+                                 double* const* u, mstopo_solve_info* infos);
+
 /* Compliances c_k = f^T u_k of the last all-realisation solve, the robust objective
  * mean(c) + kappa std(c) (population std, Sec. 4.4), and its gradient with respect to the
  * design: the self-adjoint element sensitivity -p (E0-Emin) rho_bar^(p-1) u_e^T K0 u_e

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -81,6 +82,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
   };
   h->p = *d;
   h->p.fixed = nullptr;
+  if (cudaGetDevice(&h->device) != cudaSuccess) h->device = 0;
   bool ok = d->nelx > 0 && d->nely > 0 && d->H >= 2 && d->nelx % d->H == 0 && d->nely % d->H == 0 &&
             d->nelx / d->H >= 2 && d->nely / d->H >= 2 && d->n_eig >= 1 && d->n_eig <= MSTOPO_MAX_EIG &&
             d->nu >= 0.0 && d->nu < 0.5 && d->Emin > 0.0 && d->Emin <= d->E0 && d->fixed != nullptr &&
@@ -438,3 +440,67 @@ mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- batches
+// Runs job(b) for b in [0, n) on up to 16 host threads (each bound to the handle's device);
+// every handle's work stays on its own stream, so kernels of different instances overlap
+// on the GPU.  Falls back to one thread if threads cannot be started.
+template <typename Job>
+static void run_batch(mstopo_handle* const* hs, int n, Job job) {
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int b; (b = next.fetch_add(1)) < n;) {
+      cudaSetDevice(hs[b]->device);
+      job(b);
+    }
+  };
+  std::vector<std::thread> pool;
+  const int nt = std::min(n, 16);
+  try {
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  } catch (...) {
+  }
+  work();
+  for (auto& th : pool) th.join();
+}
+
+static mstopo_status check_batch(mstopo_handle* const* hs, int32_t n) {
+  if (!hs || n < 1) return MSTOPO_INVALID_ARG;
+  for (int b = 0; b < n; ++b) {
+    if (!hs[b]) return MSTOPO_INVALID_ARG;
+    for (int c = 0; c < b; ++c)
+      if (hs[c] == hs[b]) {
+        hs[b]->err = "a handle appears twice in the batch";
+        return MSTOPO_INVALID_ARG;
+      }
+  }
+  return MSTOPO_OK;
+}
+
+mstopo_status mstopo_batch_build_preconditioner(mstopo_handle* const* hs, int32_t n, int32_t ref,
+                                                mstopo_build_info* infos) {
+  mstopo_status st0 = check_batch(hs, n);
+  if (st0 != MSTOPO_OK) return st0;
+  std::vector<mstopo_status> st(n, MSTOPO_OK);
+  run_batch(hs, n, [&](int b) {
+    st[b] = mstopo_build_preconditioner(hs[b], ref, infos ? infos + b : nullptr);
+  });
+  for (int b = 0; b < n; ++b)
+    if (st[b] != MSTOPO_OK) return st[b];
+  return MSTOPO_OK;
+}
+
+mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const double* const* f,
+                                 double* const* u, mstopo_solve_info* infos) {
+  mstopo_status st0 = check_batch(hs, n);
+  if (st0 != MSTOPO_OK) return st0;
+  if (!f || !u) return MSTOPO_INVALID_ARG;
+  std::vector<mstopo_status> st(n, MSTOPO_OK);
+  run_batch(hs, n, [&](int b) {
+    st[b] = mstopo_solve(hs[b], -1, f[b], u[b], nullptr,
+                         infos ? infos + (size_t)b * MSTOPO_MAX_SYS : nullptr);
+  });
+  for (int b = 0; b < n; ++b)
+    if (st[b] != MSTOPO_OK) return st[b];
+  return MSTOPO_OK;
+}

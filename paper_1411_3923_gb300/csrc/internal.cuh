@@ -178,6 +178,7 @@ struct Solver {
 
 struct mstopo_handle {
   mstopo_problem p{};
+  int device = 0;                   // CUDA device current at creation
   cudaStream_t s = nullptr;
   int nelx = 0, nely = 0;
   long long n_nodes = 0, n_dof = 0, n_el = 0;

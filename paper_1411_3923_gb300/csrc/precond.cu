@@ -1472,13 +1472,14 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
   const long long blk = 2LL * pc.rpc * pc.nbs;
   const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * patch_rs<T>(R)) * sizeof(T);
   (void)nb;
-  // the shared-memory limit is raised once per instantiation (never inside a graph capture)
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory limit is raised once per instantiation and device thread (never inside
+  // a graph capture: the first apply of a solve runs uncaptured)
+  static std::atomic<int> attr_set{0};
+  if (!attr_set.load()) {
     cudaError_t e = cudaFuncSetAttribute(k_patch_solve_f<T, Q, NBUF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(1);
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
   const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;

@@ -67,7 +67,8 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_build_preconditioner", "mstopo_solve", "mstopo_solve_host",
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
            "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
-           "mstopo_get_stats", "mstopo_apply_K_f32_noalloc"]
+           "mstopo_get_stats", "mstopo_apply_K_f32_noalloc", "mstopo_batch_build_preconditioner",
+           "mstopo_batch_solve"]
 
 
 def load(path: str = LIB_PATH):
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
         "mstopo_get_eigenpairs": ([vp, i32, i32, vp, vp, vp], i32),
         "mstopo_set_profiling": ([vp, i32], i32),
         "mstopo_get_stats": ([vp, C.POINTER(_Stats)], i32),
+        "mstopo_batch_build_preconditioner": ([C.POINTER(vp), i32, i32, vp], i32),
+        "mstopo_batch_solve": ([C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), vp], i32),
         "mstopo_apply_K_f32_noalloc": ([vp, vp, vp, vp, i32, i32, dbl, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -291,3 +294,38 @@ class RobustCompliance(torch.autograd.Function):
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
         return grad_out * g, None, None, None, None, None, None, None
+
+
+def _batch_handles(problems):
+    hs = (C.c_void_p * len(problems))(*[p._h for p in problems])
+    return hs
+
+
+def batch_build_preconditioner(problems, ref: int = -1) -> list:
+    """Build the preconditioners of independent problems concurrently."""
+    n = len(problems)
+    infos = (_BuildInfo * n)()
+    st = _lib.mstopo_batch_build_preconditioner(_batch_handles(problems), n, ref, infos)
+    out = [{f: getattr(infos[b], f) for f, _ in _BuildInfo._fields_} for b in range(n)]
+    if st != 0:
+        raise MstopoError(st, "batch build: " + "; ".join(
+            _lib.mstopo_last_error(p._h).decode() for p in problems))
+    return out
+
+
+def batch_solve(problems, fs):
+    """Solve all realisations of independent problems concurrently (one stream and host
+    thread per problem).  fs: one device load vector per problem.  Returns (us, infos)."""
+    n = len(problems)
+    fs = [_dev(f) for f in fs]
+    us = [torch.empty((p.n_eta, p.nely + 1, p.nelx + 1, 2), dtype=torch.float64, device=f.device)
+          for p, f in zip(problems, fs)]
+    fp = (C.c_void_p * n)(*[_ptr(f) for f in fs])
+    up = (C.c_void_p * n)(*[_ptr(u) for u in us])
+    infos = (_SolveInfo * (4 * n))()
+    st = _lib.mstopo_batch_solve(_batch_handles(problems), n, fp, up, infos)
+    out = [[{f: getattr(infos[4 * b + k], f) for f, _ in _SolveInfo._fields_}
+            for k in range(p.n_eta)] for b, p in enumerate(problems)]
+    if st != 0:
+        raise MstopoError(st, f"batch solve: {out}")
+    return us, out

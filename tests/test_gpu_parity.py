@@ -244,3 +244,29 @@ def test_solve_with_blocktri_coarse_solver(precision):
         ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
         assert msfem.energy_error(Kf, ur, ug) < 1e-6
         assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
+
+
+def test_batch_solve_matches_single_solves_and_oracle():
+    """Independent problems of uneven sizes solved concurrently (one stream and host thread
+    each): every instance equals its own single solve bit for bit (same kernels, fixed
+    reduction order) and the oracle's direct solve."""
+    m = _gpu()
+    shapes = [(48, 16, 1), (64, 32, 3), (32, 16, 1), (96, 32, 3), (64, 16, 1)]
+    wls = [workloads.small(nx, ny, seed=20 + b, kind="voids", bc="cantilever", H=8, n_eig=4,
+                           etas=(0.5,) if ne == 1 else (0.3, 0.5, 0.7), rmin=2.0, beta=8.0)
+           for b, (nx, ny, ne) in enumerate(shapes)]
+    probs = []
+    for wl in wls:
+        p = make_problem(m, wl, "mixed", tol=1e-10)
+        p.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+        probs.append(p)
+    m.batch_build_preconditioner(probs)
+    us, infos = m.batch_solve(probs, [cuda(wl.force) for wl in wls])
+    for b, (p, wl) in enumerate(zip(probs, wls)):
+        u1, inf1 = p.solve(cuda(wl.force), -1)
+        assert torch.equal(u1, us[b])
+        assert [i["iterations"] for i in inf1] == [i["iterations"] for i in infos[b]]
+        ref = pipeline.run(wl, "direct", with_grad=False)
+        for k, inf in enumerate(infos[b]):
+            assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+            assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
