@@ -83,6 +83,10 @@ typedef struct {
                                 (s >= 0, 0 = exact local solves)                            */
   void* stream;              /* cudaStream_t for all work of this handle, NULL = default   */
   int32_t coarse_solver;     /* mstopo_coarse_solver for the coarse problem K_c u_c = r_c  */
+  int32_t reuse_preconditioner; /* nonzero: mstopo_set_design keeps the preconditioner last
+                                built (on an earlier design, with the same number of
+                                realisations) instead of requiring a new build -- the basis
+                                re-use of Sec. 5.1-5.2; solves still stop on the true residual */
 } mstopo_problem;
 
 typedef struct {

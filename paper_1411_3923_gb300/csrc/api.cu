@@ -210,7 +210,7 @@ mstopo_status mstopo_set_design(mstopo_handle* h, const double* rho, int64_t n_d
   CKA(cudaStreamSynchronize(h->s));
   h->design_ready = flag ? 0 : 1;
   h->u_all_ready = 0;
-  h->pc.built = 0;
+  if (!(h->p.reuse_preconditioner && h->pc.built && h->pc.nsv == n_eta && !flag)) h->pc.built = 0;
   if (flag) {
     h->err = "design contains NaN or Inf";
     return MSTOPO_NONFINITE;

@@ -34,7 +34,7 @@ class _Problem(C.Structure):
                 ("H", C.c_int32), ("n_eig", C.c_int32), ("lambda_thresh", C.c_double),
                 ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("local_shift", C.c_double), ("stream", C.c_void_p),
-                ("coarse_solver", C.c_int32)]
+                ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32)]
 
 
 class _BuildInfo(C.Structure):
@@ -134,14 +134,16 @@ class Problem:
                  E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
                  n_eig: int = 4, lambda_thresh: float = 0.0, precision: str = "mixed",
                  tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
-                 stream: Optional[int] = None, coarse_solver: str = "auto"):
+                 stream: Optional[int] = None, coarse_solver: str = "auto",
+                 reuse_preconditioner: bool = False):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
         assert self._fixed.size == 2 * (nelx + 1) * (nely + 1)
         d = _Problem(nelx, nely, nu, E0, Emin, penal, self._fixed.ctypes.data, H, n_eig,
                      lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
-                     local_shift, stream, COARSE_SOLVERS[coarse_solver])
+                     local_shift, stream, COARSE_SOLVERS[coarse_solver],
+                     1 if reuse_preconditioner else 0)
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:

@@ -151,7 +151,8 @@ def make(name: str, scale: int = 1) -> Workload:
         return Workload(name, nelx, nely, rho, None, fixed, force, rmin=3.0, beta=16.0,
                         etas=(0.3, 0.5, 0.7), H=32, n_eig=6)
     if name == "mbb_c5":
-        nelx, nely = 3200 // scale, 4096 // scale
+        # reduced copies keep whole 32-element cells (and coarse cells)
+        nelx, nely = max(64, 3200 // scale // 32 * 32), max(64, 4096 // scale // 32 * 32)
         cell = circular_void_cell(32, 10.0)
         fixed, force = mbb_bc(nelx, nely)
         return Workload(name, nelx, nely, cell, (32, 32), fixed, force, rmin=3.0, beta=8.0,
