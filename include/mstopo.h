@@ -186,9 +186,17 @@ mstopo_status mstopo_compliance_and_sensitivity(mstopo_handle* h, double kappa, 
  * precision (MSTOPO_MIXED = FP32 arithmetic and FP32 vectors).  u, y: DEVICE nodal layout. */
 mstopo_status mstopo_apply_K(mstopo_handle* h, int32_t realisation, int32_t precision,
                              const double* u, double* y);
-/* Same, on vectors already stored in FP32 (DEVICE, nodal layout, float).  No conversions:
- * this is the kernel the MIXED flexible CG runs. */
+/* Same, on vectors already stored in FP32 (DEVICE, nodal layout, float, 8-byte aligned).
+ * No conversions: this is the kernel the MIXED flexible CG runs.  Errors: INVALID_ARG (NULL
+ * or misaligned pointer, realisation out of range), NOT_READY. */
 mstopo_status mstopo_apply_K_f32(mstopo_handle* h, int32_t realisation, const float* u, float* y);
+/* As mstopo_apply_K_f32, and realisation -1 applies every realisation's K to its own vector
+ * (n_sys vectors back to back in u and y, one launch, as in the batched solve).
+ * flags: MSTOPO_INPUT_MASKED = the caller guarantees u is zero at the Dirichlet DOFs (as the
+ * flexible-CG directions are), so the input mask is not read. */
+#define MSTOPO_INPUT_MASKED 1
+mstopo_status mstopo_apply_K_f32_ex(mstopo_handle* h, int32_t realisation, const float* u, float* y,
+                                    int32_t flags);
 /* z = M^-1 r with the built two-level preconditioner (coarse + overlapping patch solves),
  * in the given precision.  part: 0 = both levels, 1 = coarse only R_c^T K_c^-1 R_c r,
  * 2 = patches only.  r, z: DEVICE nodal layout. */

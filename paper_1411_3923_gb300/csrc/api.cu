@@ -357,13 +357,23 @@ mstopo_status mstopo_apply_K(mstopo_handle* h, int32_t realisation, int32_t prec
 }
 
 mstopo_status mstopo_apply_K_f32(mstopo_handle* h, int32_t realisation, const float* u, float* y) {
+  return mstopo_apply_K_f32_ex(h, realisation, u, y, 0);
+}
+
+mstopo_status mstopo_apply_K_f32_ex(mstopo_handle* h, int32_t realisation, const float* u, float* y,
+                                    int32_t flags) {
   if (!h) return MSTOPO_INVALID_ARG;
   if (!h->design_ready) { h->err = "no design set"; return MSTOPO_NOT_READY; }
   CHECK_ARG(u && y, "null pointer");
-  CHECK_ARG(realisation >= 0 && realisation < h->n_eta, "realisation out of range");
+  CHECK_ARG(realisation >= -1 && realisation < h->n_eta, "realisation out of range");
+  CHECK_ARG((flags & ~MSTOPO_INPUT_MASKED) == 0, "unknown flag");
+  CHECK_ARG((reinterpret_cast<uintptr_t>(u) & 7) == 0 && (reinterpret_cast<uintptr_t>(y) & 7) == 0,
+            "u and y must be 8-byte aligned (float2 nodes)");
+  const int sys0 = realisation < 0 ? 0 : realisation;
+  const int nsys = realisation < 0 ? h->n_eta : 1;
   cudaEvent_t pa = prof_begin(h->prof, h->s);
-  CKA(launch_matvec_f32(u, y, h->d_E32 + realisation * h->n_el, h->d_nmask, h->nelx, h->nely,
-                        h->st32, 1, h->n_dof, h->n_el, h->s));
+  CKA(launch_matvec_f32(u, y, h->d_E32 + sys0 * h->n_el, h->d_nmask, h->nelx, h->nely, h->st32,
+                        nsys, h->n_dof, h->n_el, h->s, !(flags & MSTOPO_INPUT_MASKED)));
   prof_end(h->prof, PROF_MATVEC32, pa, h->s);
   CKA(cudaStreamSynchronize(h->s));
   return MSTOPO_OK;

@@ -68,7 +68,7 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
            "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
            "mstopo_get_stats", "mstopo_apply_K_f32_noalloc", "mstopo_batch_build_preconditioner",
-           "mstopo_batch_solve"]
+           "mstopo_batch_solve", "mstopo_apply_K_f32_ex"]
 
 
 def load(path: str = LIB_PATH):
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "mstopo_get_stats": ([vp, C.POINTER(_Stats)], i32),
         "mstopo_batch_build_preconditioner": ([C.POINTER(vp), i32, i32, vp], i32),
         "mstopo_batch_solve": ([C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), vp], i32),
+        "mstopo_apply_K_f32_ex": ([vp, i32, vp, vp, i32], i32),
         "mstopo_apply_K_f32_noalloc": ([vp, vp, vp, vp, i32, i32, dbl, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -237,10 +238,14 @@ class Problem:
         self._check(_lib.mstopo_apply_K(self._h, realisation, precision, _ptr(u), _ptr(y)))
         return y
 
-    def apply_K_f32(self, u: torch.Tensor, realisation: int = 0, out: Optional[torch.Tensor] = None):
+    def apply_K_f32(self, u: torch.Tensor, realisation: int = 0, out: Optional[torch.Tensor] = None,
+                    input_masked: bool = False):
+        """FP32 matvec; realisation -1 = all realisations (vectors back to back).
+        input_masked: u is already zero at the Dirichlet DOFs (the input mask is skipped)."""
         u = _dev(u, torch.float32)
         y = torch.empty_like(u) if out is None else out
-        self._check(_lib.mstopo_apply_K_f32(self._h, realisation, _ptr(u), _ptr(y)))
+        self._check(_lib.mstopo_apply_K_f32_ex(self._h, realisation, _ptr(u), _ptr(y),
+                                               1 if input_masked else 0))
         return y
 
     def apply_precond(self, r: torch.Tensor, precision: int = FP64, part: int = 0) -> torch.Tensor:
