@@ -449,10 +449,99 @@ def run_gradcheck(args):
                       "entries": rows}))
 
 
+def run_workload(args):
+    """The whole path on one named workload (no L2 flush, wall and event times): design chain,
+    preconditioner build, MIXED solve of all realisations (and FP64 unless --workload-mixed-only),
+    robust compliance and design gradient.  'cantilever_batch' runs the 64-instance uneven
+    batch through the batch entry points (and, beside it, the instances one after another)."""
+    import numpy as np
+    import torch
+    import workloads
+    import paper_1411_3923_gb300 as m
+
+    name = args.workload_run
+    out = {"workload_run": name}
+    if name == "cantilever_batch":
+        wls = workloads.cantilever_batch()
+        probs = []
+        for wl in wls:
+            p = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
+                          penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision="mixed", tol=1e-8)
+            p.set_design(torch.from_numpy(np.ascontiguousarray(wl.rho)).cuda(), wl.rmin, wl.beta,
+                         wl.etas, wl.cell)
+            probs.append(p)
+        dofs = sum(p.n_dof for p in probs)
+        torch.cuda.synchronize()
+        t = time.time()
+        binfo = m.batch_build_preconditioner(probs)
+        torch.cuda.synchronize()
+        tb = time.time() - t
+        fs = [torch.from_numpy(np.ascontiguousarray(wl.force)).cuda() for wl in wls]
+        m.batch_solve(probs, fs)   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t = time.time()
+        us, infos = m.batch_solve(probs, fs)
+        torch.cuda.synchronize()
+        ts = time.time() - t
+        t = time.time()
+        for p, f in zip(probs, fs):
+            p.solve(f, -1)
+        torch.cuda.synchronize()
+        tq = time.time() - t
+        its = [i[0]["iterations"] for i in infos]
+        out.update({"instances": len(probs), "dofs": dofs, "build_s": tb,
+                    "coarse_solvers": sorted(set(b["coarse_solver"] for b in binfo)),
+                    "batch_solve_s": ts, "batch_mdof_per_s": dofs / ts / 1e6,
+                    "sequential_solve_s": tq, "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
+                    "max_rel_residual": max(i[0]["rel_residual"] for i in infos),
+                    "all_converged": all(i[0]["status"] == 0 for i in infos)})
+        print(json.dumps(out))
+        return
+    wl = workloads.make(name)
+    f = torch.from_numpy(np.ascontiguousarray(wl.force)).cuda()
+    rho = torch.from_numpy(np.ascontiguousarray(wl.rho)).cuda()
+    out.update({"mesh": [wl.nelx, wl.nely], "dofs": 2 * (wl.nelx + 1) * (wl.nely + 1),
+                "realisations": len(wl.etas)})
+    precisions = ["mixed"] if args.workload_mixed_only else ["mixed", "fp64"]
+    for prec in precisions:
+        prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
+                         penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=1e-8)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        prob.set_design(rho, wl.rmin, wl.beta, wl.etas, wl.cell)
+        info = prob.build_preconditioner()
+        torch.cuda.synchronize()
+        t1 = time.time()
+        prob.solve(f, -1)            # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        u, infos = prob.solve(f, -1)
+        torch.cuda.synchronize()
+        t3 = time.time()
+        c, fr, g = prob.compliance_and_sensitivity(1.0)
+        torch.cuda.synchronize()
+        t4 = time.time()
+        out[prec] = {"build_s": t1 - t0, "build": {k: info[k] for k in ("n_agglomerates", "n_types", "n_coarse",
+                                                                        "coarse_solver", "ms_eigen", "ms_patch_factor",
+                                                                        "ms_coarse", "ms_total")},
+                     "solve_s": t3 - t2, "solve_event_ms": infos[0]["ms"],
+                     "iterations": [i["iterations"] for i in infos],
+                     "rel_residual": [i["rel_residual"] for i in infos],
+                     "compliance": [i["compliance"] for i in infos], "f_robust": fr,
+                     "sensitivity_s": t4 - t3}
+        prob.close()
+        del prob
+        torch.cuda.empty_cache()
+    if "fp64" in out:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["solve_s"] / out["mixed"]["solve_s"]
+    print(json.dumps(out))
+
+
 def run_only(args):
     """One kernel in a short loop: 'patch' = FP32 patch solves of a workload's preconditioner
     (apply_precond, MIXED, patches only, realisation 0; default the 1024x512 workload);
-    'matvec' = FP32 matvec (default the 3200x4096 mesh, 26.2M DOFs).  --only-workload and
+    'matvec' = FP32 matvec as the flexible CG launches it (all realisations, default the
+    3200x4096 mesh, 26.2M DOFs x 3).  --only-workload and
     --only-scale pick another workload or a reduced copy of it."""
     import torch
     import paper_1411_3923_gb300 as m
@@ -468,12 +557,13 @@ def run_only(args):
         r = torch.randn((wl.nely + 1, wl.nelx + 1, 2), dtype=torch.float64, device=dev)
         for _ in range(args.reps):
             prob.apply_precond(r, m.MIXED, 2)
-    else:
-        n = prob.n_dof
-        u = torch.randn(n, device=dev, dtype=torch.float32)
+    else:   # the flexible CG's launch: every realisation, inputs zero at Dirichlet DOFs
+        import numpy as np
+        free = torch.from_numpy(~np.asarray(wl.fixed, dtype=bool).reshape(-1)).to(dev)
+        u = torch.randn(len(wl.etas), prob.n_dof, device=dev, dtype=torch.float32) * free
         y = torch.empty_like(u)
         for _ in range(args.reps):
-            prob.apply_K_f32(u, 0, y)
+            prob.apply_K_f32(u, -1, y, input_masked=True)
     torch.cuda.synchronize()
     print(json.dumps({"only": args.only, "workload": name, "scale": args.only_scale,
                       "mesh": [wl.nelx, wl.nely], "reps": args.reps, "ok": True}))
@@ -497,12 +587,19 @@ def main():
                     help="check the adjoint gradient against central differences on this many "
                          "seeded design variables (no benchmark)")
     ap.add_argument("--gradcheck-workload", default="mbb_c5")
+    ap.add_argument("--workload-run", default=None,
+                    help="run the whole path on a named workload (mbb_c1, mbb_c2, mbb_c3, mbb_c5, "
+                         "cantilever_batch) and print one JSON line (no benchmark)")
+    ap.add_argument("--workload-mixed-only", action="store_true")
     args = ap.parse_args()
     if args.only:
         run_only(args)
         return
     if args.gradcheck:
         run_gradcheck(args)
+        return
+    if args.workload_run:
+        run_workload(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

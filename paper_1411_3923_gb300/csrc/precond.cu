@@ -43,6 +43,7 @@ namespace cg = cooperative_groups;
 #define PATCH_THREADS 288   // >= ceil(hrows / 2) * PATCH_S = 33 * 8 for H = 32 (warp multiple)
 #define PATCH_COLS 16       // right-hand-side columns per CTA (patches x systems), at most
 #define PATCH_GROUP 4       // patches per CTA
+#define PATCH_PF 8          // prefetched input values per thread (nb * R <= 8 x threads)
 #define EIG_MAX_SWEEPS 80
 #define EIG_TOL 1e-7
 #define EIG_SHIFT 1e-5
@@ -781,7 +782,7 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
   constexpr int R = 4 * Q;
   constexpr int RS = patch_rs<T>(R);
   constexpr int S = PATCH_S;
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[NBUF];
   __shared__ int s_abort;
   __shared__ int s_node[PATCH_COLS];   // patch origin per column block: (I-1)H, (J-1)H packed
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -792,6 +793,7 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
   const long long blk = 2LL * hrows * nbs;
   const uint32_t bytes = (uint32_t)(blk * sizeof(T));
   T* stg = reinterpret_cast<T*>(smraw);                 // [NBUF][2][hrows][nbs]
+  static_assert(NBUF >= 1 && NBUF <= 3, "stage buffers");
   T* vb = stg + NBUF * blk;                             // [nbs][RS] input b_k or y_k
   T* prev = vb + (long long)nbs * RS;                   // [nbs][RS] y_{k-1} or x_{k+1}
   T* cur = prev + (long long)nbs * RS;                  // [nbs][RS] this line's result
@@ -823,7 +825,9 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
       mbar_expect_tx(&bars[b], bytes);
       bulk_g2s(stg + b * blk, src(b), bytes, &bars[b]);
     }
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase[NBUF];
+#pragma unroll
+  for (int b = 0; b < NBUF; ++b) phase[b] = 0u;
   // thread roles: column group cgi (columns j0 .. j0 + CPT), a pair of rows (rl, rl + hp)
   // of the half block, reduction part pp of S
   constexpr int CPT = patch_cpt(Q);
@@ -837,30 +841,52 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
     prev[q] = T(0);
     cur[q] = T(0);
   }
+  // The input vector of every line is loaded into registers while the previous line computes
+  // (PATCH_PF values per thread): forward lines gather r, backward lines read y_k from the
+  // work buffer; the first backward line takes y_{NL-1} from shared memory (just computed).
+  T pf[PATCH_PF];
+  auto load_line = [&](int ls) {
+    const bool fw = ls < NL;
+    const int k = fw ? ls : NL - 1 - (ls - NL);
+#pragma unroll
+    for (int i = 0; i < PATCH_PF; ++i) {
+      const int q = threadIdx.x + i * blockDim.x;
+      T v = T(0);
+      if (q < nb * R) {
+        if (fw) {
+          const int c = q / R, p = q % R;
+          if (p < cnt && fr[(long long)k * nb + c]) {
+            const int ia = s_node[p];
+            const int I = ia % (ncx + 1), J = ia / (ncx + 1);
+            const int x = (I - 1) * H + (c >> 1), y = (J - 1) * H + k;
+            if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
+              v = rs[2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
+          }
+        } else {
+          v = X[(long long)k * nb * R + q];
+        }
+      }
+      pf[i] = v;
+    }
+  };
+  load_line(0);
   int m = 0;
   for (int ls = 0; ls < 2 * NL; ++ls) {
     const bool fw = ls < NL;
     const int k = fw ? ls : NL - 1 - (ls - NL);
     const bool has_prev = fw ? (k > 0) : (k < NL - 1);
     // input vector of the line
-    if (fw) {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) {
-        const int c = q / R, p = q % R;
-        T v = T(0);
-        if (p < cnt && fr[(long long)k * nb + c]) {
-          const int ia = s_node[p];
-          const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-          const int x = (I - 1) * H + (c >> 1), y = (J - 1) * H + k;
-          if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
-            v = rs[2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
-        }
-        vb[c * RS + p] = v;
-      }
+    if (ls == NL) {
+      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[(q / R) * RS + q % R] = prev[(q / R) * RS + q % R];
     } else {
-      const T* yk = X + (long long)k * nb * R;
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[(q / R) * RS + q % R] = yk[q];
+#pragma unroll
+      for (int i = 0; i < PATCH_PF; ++i) {
+        const int q = threadIdx.x + i * blockDim.x;
+        if (q < nb * R) vb[(q / R) * RS + q % R] = pf[i];
+      }
     }
     __syncthreads();
+    if (ls + 1 < 2 * NL && ls + 1 != NL) load_line(ls + 1);
     for (int half = 0; half < 2; ++half, ++m) {
       const int b = m % NBUF;
       if (threadIdx.x == 0 && !s_abort && !mbar_wait(&bars[b], phase[b])) {
@@ -1468,6 +1494,7 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
                                 const T* bwd, T* Xg) {
   Precond& pc = h->pc;
   const int nb = pc.nbP, R = 4 * Q;
+  // stage buffers: FP32 two (the next half-stage loads while one is used), FP64 one
   constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
   const long long blk = 2LL * pc.rpc * pc.nbs;
   const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * patch_rs<T>(R)) * sizeof(T);
