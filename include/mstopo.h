@@ -73,7 +73,7 @@ typedef struct {
   double nu;                 /* Poisson's ratio, 0 <= nu < 0.5                             */
   double E0, Emin, penal;    /* modified SIMP: E = Emin + (E0 - Emin) rho_bar^penal (Sec. 2.2) */
   const uint8_t* fixed;      /* HOST, nodal layout of uint8: nonzero = Dirichlet DOF (u = 0) */
-  int32_t H;                 /* coarse cell edge in elements (Sec. 2.4); agglomerates are 2H x 2H */
+  int32_t H;                 /* coarse cell edge in elements, 2..32 (Sec. 2.4); agglomerates are 2H x 2H */
   int32_t n_eig;             /* eigenvectors kept per agglomerate (cap when lambda_thresh > 0), 1..16 */
   double lambda_thresh;      /* > 0: keep only eigenvalues below it (Sec. 2.4, lambda_Omega) */
   int32_t precision;         /* mstopo_precision                                           */
@@ -111,7 +111,7 @@ typedef struct {
 } mstopo_solve_info;
 
 /* Create a handle for one mesh and boundary-condition set; allocates its device workspace.
- * Errors: INVALID_ARG (sizes not multiples of H, H < 2, nelx/H < 2 or nely/H < 2, n_eig
+ * Errors: INVALID_ARG (sizes not multiples of H, H outside 2..32, nelx/H < 2 or nely/H < 2, n_eig
  * outside 1..16, nu outside [0, 0.5), Emin <= 0 or Emin > E0, fixed == NULL),
  * OUT_OF_MEMORY, CUDA_ERROR.  *out is NULL on failure. */
 mstopo_status mstopo_create(const mstopo_problem* desc, mstopo_handle** out);

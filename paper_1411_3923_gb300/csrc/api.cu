@@ -87,7 +87,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             d->nelx / d->H >= 2 && d->nely / d->H >= 2 && d->n_eig >= 1 && d->n_eig <= MSTOPO_MAX_EIG &&
             d->nu >= 0.0 && d->nu < 0.5 && d->Emin > 0.0 && d->Emin <= d->E0 && d->fixed != nullptr &&
             d->tol > 0.0 && d->max_iter > 0 && d->local_shift >= 0.0 &&
-            (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 64 &&
+            (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 32 &&
             d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI;
   if (!ok) {
     h->err = "invalid problem description";

@@ -39,8 +39,7 @@ namespace cg = cooperative_groups;
 #define SOLVE_THREADS 320   // 160 rows x 2 threads per pass covers nb = 2(2H+1) up to H = 39
 #define EIG_CL 4            // CTAs per agglomerate type in the eigen-solve (subspace columns split)
 #define PATCH_HALVES 2      // row halves of every line in the patch solve
-#define PATCH_S 8           // threads sharing one row pair in the patch solve
-#define PATCH_THREADS 288   // >= ceil(hrows / 2) * PATCH_S = 33 * 8 for H = 32 (warp multiple)
+#define PATCH_MAX_HP 33     // row pairs per half-stage the patch solve covers: H <= 32
 #define PATCH_COLS 16       // right-hand-side columns per CTA (patches x systems), at most
 #define PATCH_GROUP 4       // patches per CTA
 #define PATCH_PF 8          // prefetched input values per thread (nb * R <= 8 x threads)
@@ -759,10 +758,16 @@ __device__ __forceinline__ void load_vec(const T* p, T* v) {
 // Groups g0 + blockIdx.x; a group is up to R agglomerates of one type in one realisation
 // (column p = agglomerate p of the group); its right-hand sides come from system
 // grp_sys[g] - sys0 of r.  The R columns are split over patch_cg(Q) thread groups of
-// PATCH_THREADS threads (patch_cpt(Q) columns each), which multiplies the warps that hide
+// patch_threads(Q) threads (patch_cpt(Q) columns each), which multiplies the warps that hide
 // the shared-memory latency of the row products.
 __host__ __device__ constexpr int patch_cpt(int Q) { return Q == 4 ? 8 : 4; }
 __host__ __device__ constexpr int patch_cg(int Q) { return 4 * Q / patch_cpt(Q); }
+// threads sharing one row pair (16 with a 4-deeper reduction was slower at four columns);
+// threads of one column group (a warp multiple)
+__host__ __device__ constexpr int patch_s(int) { return 8; }
+__host__ __device__ constexpr int patch_threads(int Q) {
+  return (PATCH_MAX_HP * patch_s(Q) + 31) / 32 * 32;
+}
 // Row stride of the right-hand-side vectors in shared memory: the 8 lanes that share a row
 // pair read 8 consecutive rows with 16-byte loads, which are bank-conflict free when a row
 // is an odd number of 16-byte chunks.
@@ -772,7 +777,7 @@ __host__ __device__ constexpr int patch_rs(int R) {
 }
 
 template <typename T, int Q, int NBUF>
-__global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
+__global__ void __launch_bounds__(patch_threads(Q) * patch_cg(Q)) k_patch_solve_f(
     const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
     int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
     const int* __restrict__ grp_first, const int* __restrict__ grp_count,
@@ -781,7 +786,8 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
     T* __restrict__ Xg, int* __restrict__ err) {
   constexpr int R = 4 * Q;
   constexpr int RS = patch_rs<T>(R);
-  constexpr int S = PATCH_S;
+  constexpr int S = patch_s(Q);
+  constexpr int GT = patch_threads(Q);
   __shared__ __align__(8) uint64_t bars[NBUF];
   __shared__ int s_abort;
   __shared__ int s_node[PATCH_COLS];   // patch origin per column block: (I-1)H, (J-1)H packed
@@ -831,7 +837,7 @@ __global__ void __launch_bounds__(PATCH_THREADS * patch_cg(Q)) k_patch_solve_f(
   // thread roles: column group cgi (columns j0 .. j0 + CPT), a pair of rows (rl, rl + hp)
   // of the half block, reduction part pp of S
   constexpr int CPT = patch_cpt(Q);
-  const int cgi = threadIdx.x / PATCH_THREADS, t = threadIdx.x % PATCH_THREADS;
+  const int cgi = threadIdx.x / GT, t = threadIdx.x % GT;
   const int j0 = cgi * CPT;
   const int pp = t % S, rl = t / S;
   const int hp = (hrows + 1) >> 1;
@@ -1272,11 +1278,25 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaEventRecord(ev[2], s));
 
   // 3. patch factors: W_k, V_k and the packed stage blocks (FP64 and FP32)
+  // patches per work group (see step 5): it fixes the patch kernel's thread mapping
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int P = std::max(1, std::min(PATCH_COLS, (pc.Nc * nsv + sms - 1) / std::max(sms, 1)));
+  const int Qp = (P + 3) / 4;
   pc.rpc = (nbP + PATCH_HALVES - 1) / PATCH_HALVES;
-  // factor row stride: a multiple of 4 with stride = 8 (mod 32) floats, so that the four row
-  // pairs a warp reads in one shared load fall on disjoint banks
+  if ((pc.rpc + 1) / 2 > PATCH_MAX_HP) {
+    h->err = "H > 32 is not supported by the patch solve";
+    return MSTOPO_INVALID_ARG;
+  }
+  // factor row stride: a multiple of 4 that puts the rows one warp reads in one shared load
+  // on disjoint banks: 4 row pairs x 8 lanes (stride = 8 mod 32 floats) or 2 row pairs x 16
+  // lanes (stride = 16 mod 32)
   pc.nbs = (nbP + 3) / 4 * 4;
-  while (pc.nbs % 32 != 8) pc.nbs += 4;
+  while (pc.nbs % 32 != (patch_s(Qp) == 16 ? 16 : 8)) pc.nbs += 4;
   {
     const double* pLi = dLi + (size_t)T * NA * nnA;
     const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
@@ -1413,13 +1433,6 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   std::vector<std::vector<int>> by_type(T);
   for (int i = 0; i < pc.Nc; ++i) by_type[pc.h_type_of_agg[i]].push_back(i);
   std::vector<int> perm, gt, gf, gc, gs, agg_group((size_t)nsv * pc.Nc), agg_slot((size_t)nsv * pc.Nc);
-  int sms = 152;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int P = std::max(1, std::min(PATCH_COLS, (pc.Nc * nsv + sms - 1) / std::max(sms, 1)));
   pc.patches_per_group = P;
   pc.h_grp_begin.assign(nsv + 1, 0);
   for (int k = 0; k < nsv; ++k) {
@@ -1510,7 +1523,7 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
   const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;
-  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, PATCH_THREADS * patch_cg(Q), sm, h->s>>>(
+  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, patch_threads(Q) * patch_cg(Q), sm, h->s>>>(
       r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_sys,
       pc.d_grp_first, pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
       h->d_flag + 1);
