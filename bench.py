@@ -40,6 +40,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: 152 SMs x 2 FP64 FMA/clk (measured 1.19 TFLOP/s at ~1.95 GHz) x 2 x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one FP32 patch-solve launch on the 1024x512 workload, from an
+# ncu capture of `bench.py --only patch` (dram__bytes_read.sum + dram__bytes_write.sum of the
+# current kernel); None once the kernel changes
+PATCH_TRAFFIC_BYTES = 294.4e6 + 26.6e6
 
 
 def load_peaks():
@@ -266,7 +270,7 @@ def run_ours(args, rank: int, world: int):
         cand.append((kern["patch_solve"]["ms"], {
             "kernel": "k_patch_solve<float>", "bound": "alu", "achieved": ach,
             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-            "traffic": None, "avg_launch_ms": t,
+            "traffic": PATCH_TRAFFIC_BYTES, "traffic_unit": "B per launch (ncu)", "avg_launch_ms": t,
             "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz"}))
     if kern["matvec_f32"]["launches"]:
         t = kern["matvec_f32"]["ms"] / kern["matvec_f32"]["launches"]
