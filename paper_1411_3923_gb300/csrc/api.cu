@@ -103,6 +103,13 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     }
     h->s = h->own_stream;
   }
+  // side stream and events of the preconditioner's fork (coarse chain beside the patch solve)
+  if (cudaStreamCreateWithFlags(&h->s_side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    h->err = "could not create the side stream";
+    return fail(MSTOPO_CUDA_ERROR);
+  }
   if (getenv("MSTOPO_NO_GRAPHS")) h->graphs_enabled = 0;
   h->nelx = d->nelx;
   h->nely = d->nely;
@@ -151,6 +158,9 @@ void mstopo_destroy(mstopo_handle* h) {
                   h->d_f_all, h->d_host_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s_side) cudaStreamDestroy(h->s_side);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }

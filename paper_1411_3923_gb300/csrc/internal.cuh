@@ -207,6 +207,8 @@ struct mstopo_handle {
   double* d_host_stage = nullptr;   // device staging for the host-pointer entry point
   Prof prof;
   cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
+  cudaStream_t s_side = nullptr;      // side stream of the preconditioner's coarse chain
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs_enabled = 1;
   long long pc_generation = 0;        // bumped by every preconditioner build
   FcgGraph fcg_graph;

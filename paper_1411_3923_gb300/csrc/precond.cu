@@ -1536,21 +1536,43 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
   Precond& pc = h->pc;
   cudaStream_t s = h->s;
   const long long n = h->n_dof;
-  if (part != 2) {
-    note_launch(), k_restrict<T><<<dim3(pc.Nc, nsys), PC_THREADS, 0, s>>>(r, n, h->nelx, h->nely, pc.H, pc.ncx,
-                                                          pc.d_type_of_agg, pc.d_kept, pc.d_coff,
-                                                          psi, pc.kmax, pc.d_rc, pc.Nt);
-    cudaEvent_t pa = prof_begin(h->prof, s);
-    if (pc.coarse_mode == MSTOPO_COARSE_BLOCKTRI) {
+  // With both levels, the restriction (and the dense coarse solve) run on the side stream
+  // beside the patch solve, which leaves registers and threads free on every SM; the
+  // cooperative block sweeps need the whole GPU and follow the join on the main stream.
+  const bool fork = part == 0 && h->s_side != nullptr;
+  const bool dense = pc.coarse_mode != MSTOPO_COARSE_BLOCKTRI;
+  cudaStream_t sc = fork ? h->s_side : s;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(h->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, h->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+  }
+  auto coarse_solve = [&](cudaStream_t st) -> cudaError_t {
+    cudaEvent_t pa = prof_begin(h->prof, st);
+    if (!dense) {
       const long long so = (long long)sys0 * pc.NLc * pc.nbc * pc.nbc;
       cudaError_t e = coarse_bt_apply(pc.d_cLinv + so, pc.d_cLinvT + so, pc.d_cW + so, pc.d_cV + so,
                                       pc.d_s2o, pc.nbc, pc.NLc, pc.Nt, pc.d_rc, pc.d_uc, nsys,
-                                      pc.d_cy, pc.d_cx, pc.d_cbar, h->d_flag + 1, pc.sweep_grid, s);
+                                      pc.d_cy, pc.d_cx, pc.d_cbar, h->d_flag + 1, pc.sweep_grid, st);
       if (e != cudaSuccess) return e;
     } else {
-      note_launch(), k_coarse_gemv<<<dim3(cdiv((long long)pc.Nt * 32, 256), nsys), 256, 0, s>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, sys0);
+      note_launch(), k_coarse_gemv<<<dim3(cdiv((long long)pc.Nt * 32, 256), nsys), 256, 0, st>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, sys0);
     }
-    prof_end(h->prof, PROF_COARSE, pa, s);
+    prof_end(h->prof, PROF_COARSE, pa, st);
+    return cudaGetLastError();
+  };
+  if (part != 2) {
+    note_launch(), k_restrict<T><<<dim3(pc.Nc, nsys), PC_THREADS, 0, sc>>>(r, n, h->nelx, h->nely, pc.H, pc.ncx,
+                                                          pc.d_type_of_agg, pc.d_kept, pc.d_coff,
+                                                          psi, pc.kmax, pc.d_rc, pc.Nt);
+    if (!fork || dense) {
+      cudaError_t e = coarse_solve(sc);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (fork) {
+    cudaError_t e = cudaEventRecord(h->ev_join, sc);
+    if (e != cudaSuccess) return e;
   }
   int Rcols = 4;
   if (part != 1) {
@@ -1566,6 +1588,14 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
     }
     if (e != cudaSuccess) return e;
     prof_end(h->prof, PROF_PATCH, pa, s);
+  }
+  if (fork) {
+    cudaError_t e = cudaStreamWaitEvent(s, h->ev_join, 0);
+    if (e != cudaSuccess) return e;
+    if (!dense) {
+      e = coarse_solve(s);
+      if (e != cudaSuccess) return e;
+    }
   }
   note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, sys0, pc.Nc, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
