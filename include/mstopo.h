@@ -180,6 +180,16 @@ mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const doub
 mstopo_status mstopo_compliance_and_sensitivity(mstopo_handle* h, double kappa, double* c,
                                                 double* f_robust, double* dfdrho);
 
+/* ---- failure injection (tests of the bounded device waits) --------------------------- */
+/* MSTOPO_INJECT_SWEEP_STALL: the next preconditioner application that runs the block-
+ * tridiagonal coarse sweeps makes their first grid barrier wait for one arrival too many.
+ * The barrier's bounded wait gives up (about half a second), the call returns
+ * MSTOPO_TIMEOUT, nothing faults or hangs, and the handle stays usable.  Errors:
+ * INVALID_ARG (unknown injection). */
+#define MSTOPO_INJECT_NONE 0
+#define MSTOPO_INJECT_SWEEP_STALL 1
+mstopo_status mstopo_inject(mstopo_handle* h, int32_t what);
+
 /* ---- kernel-level entry points (verification and measurement) --------------------- */
 
 /* y = K(E_k) u on the free DOFs, matrix-free element by element (Sec. 2.1), in the given

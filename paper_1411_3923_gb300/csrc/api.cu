@@ -524,3 +524,10 @@ mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const doub
     if (st[b] != MSTOPO_OK) return st[b];
   return MSTOPO_OK;
 }
+
+mstopo_status mstopo_inject(mstopo_handle* h, int32_t what) {
+  if (!h) return MSTOPO_INVALID_ARG;
+  CHECK_ARG(what == MSTOPO_INJECT_NONE || what == MSTOPO_INJECT_SWEEP_STALL, "unknown injection");
+  h->inject = what;
+  return MSTOPO_OK;
+}

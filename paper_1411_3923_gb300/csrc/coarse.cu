@@ -227,8 +227,7 @@ cudaError_t coarse_bt_factor(const double* A, const double* B, int nb, int NL, d
   const int np = (nb + CB_TILE - 1) / CB_TILE;
   const size_t ti_smem = (size_t)nb * TI_W * sizeof(double);
   if (ti_smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ti_smem);
+    cudaError_t e = smem_limit_max<k_tri_inv>();
     if (e != cudaSuccess) return e;
   }
   cudaError_t e;
@@ -311,6 +310,7 @@ struct SweepArgs {
   unsigned int* bar;
   int* err;
   int nb, NL, Nt, nsys;
+  int stall;                            // test injection: the first barrier cannot complete
 };
 
 // Sum over the 32 lanes of a warp, all lanes receive it.
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 2) k_coarse_sweep(SweepArgs a) 
   const int nb = a.nb, NL = a.NL, ns = a.nsys;
   const long long nn = (long long)nb * nb, lines = (long long)NL * nb;
   const long long sys_stride = (long long)NL * nn;
-  unsigned int target = 0;
+  unsigned int target = a.stall ? 1u : 0u;   // an injected stall waits for one arrival too many
   // 0. gather r_c into line order (padding slots 0)
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ns * lines;
        t += (long long)gridDim.x * blockDim.x) {
@@ -449,10 +449,11 @@ cudaError_t coarse_bt_apply(const double* Linv, const double* LinvT, const doubl
                             const double* V, const int* s2o, int nb, int NL, int Nt,
                             const double* rc, double* uc, int nsys, double* ywork,
                             double* xwork, unsigned int* bar, int* err, int grid,
-                            cudaStream_t s) {
+                            int stall, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   SweepArgs a;
+  a.stall = stall;
   a.Linv = Linv; a.LinvT = LinvT; a.W = W; a.V = V; a.s2o = s2o; a.rc = rc; a.uc = uc;
   a.y = ywork; a.x = xwork; a.bar = bar; a.err = err; a.nb = nb; a.NL = NL; a.Nt = Nt;
   a.nsys = nsys;

@@ -210,6 +210,7 @@ struct mstopo_handle {
   cudaStream_t s_side = nullptr;      // side stream of the preconditioner's coarse chain
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs_enabled = 1;
+  int inject = 0;                     // test injection (mstopo_inject), consumed by its target
   long long pc_generation = 0;        // bumped by every preconditioner build
   FcgGraph fcg_graph;
 };
@@ -222,7 +223,7 @@ cudaError_t coarse_bt_apply(const double* Linv, const double* LinvT, const doubl
                             const double* V, const int* s2o, int nb, int NL, int Nt,
                             const double* rc, double* uc, int nsys, double* ywork,
                             double* xwork, unsigned int* bar, int* err, int grid,
-                            cudaStream_t s);
+                            int stall, cudaStream_t s);
 int coarse_sweep_grid();
 int coarse_sweep_max_nb(int grid, int nsys);
 
@@ -245,3 +246,22 @@ void solver_free(Solver& sv);
 
 // helpers
 inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared-memory limit to the most the device allows beside its
+// static shared memory, once per kernel (thread-safe).  Launches then pass their own size;
+// a per-call limit set by concurrent builds of different sizes would race.
+template <auto kernel>
+cudaError_t smem_limit_max() {
+  static const cudaError_t once = []() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+  }();
+  return once;
+}

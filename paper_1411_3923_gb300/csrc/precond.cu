@@ -499,7 +499,7 @@ __global__ void __cluster_dims__(EIG_CL, 1, 1) __launch_bounds__(SOLVE_THREADS) 
 
 template <int Q>
 static cudaError_t launch_eigen_q(int T, size_t esm, cudaStream_t s, const EigArgs& ea) {
-  cudaError_t e = cudaFuncSetAttribute(k_eigen<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
+  cudaError_t e = smem_limit_max<k_eigen<Q>>();
   if (e != cudaSuccess) return e;
   note_launch(), k_eigen<Q><<<T * EIG_CL, SOLVE_THREADS, esm, s>>>(ea);
   return cudaGetLastError();
@@ -1379,7 +1379,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     CKB(cudaMalloc(&pc.d_Kcinv, (size_t)nsv * Nt * Nt * 8));
     const int nblk = cdiv((long long)NLc * nbc, RC);
     CKB(cudaMalloc(&cX, (size_t)nblk * NLc * nbc * RC * 8));
-    CKB(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nbc * RC * 8));
+    CKB(smem_limit_max<k_coarse_inverse>());
     for (int k = 0; k < nsv; ++k) {
       note_launch(), k_coarse_inverse<<<nblk, PC_THREADS, 2 * nbc * RC * 8, s>>>(cLi + k * nlA, cC + k * nlB, nbc, NLc, d_s2o, Nt, cX,
                                                                                  pc.d_Kcinv + (size_t)k * Nt * Nt);
@@ -1512,14 +1512,9 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
   const long long blk = 2LL * pc.rpc * pc.nbs;
   const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * patch_rs<T>(R)) * sizeof(T);
   (void)nb;
-  // the shared-memory limit is raised once per instantiation and device thread (never inside
-  // a graph capture: the first apply of a solve runs uncaptured)
-  static std::atomic<int> attr_set{0};
-  if (!attr_set.load()) {
-    cudaError_t e = cudaFuncSetAttribute(k_patch_solve_f<T, Q, NBUF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+  {
+    cudaError_t e = smem_limit_max<k_patch_solve_f<T, Q, NBUF>>();
     if (e != cudaSuccess) return e;
-    attr_set.store(1);
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
   const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;
@@ -1553,7 +1548,9 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
       const long long so = (long long)sys0 * pc.NLc * pc.nbc * pc.nbc;
       cudaError_t e = coarse_bt_apply(pc.d_cLinv + so, pc.d_cLinvT + so, pc.d_cW + so, pc.d_cV + so,
                                       pc.d_s2o, pc.nbc, pc.NLc, pc.Nt, pc.d_rc, pc.d_uc, nsys,
-                                      pc.d_cy, pc.d_cx, pc.d_cbar, h->d_flag + 1, pc.sweep_grid, st);
+                                      pc.d_cy, pc.d_cx, pc.d_cbar, h->d_flag + 1, pc.sweep_grid,
+                                      h->inject == MSTOPO_INJECT_SWEEP_STALL, st);
+      if (h->inject == MSTOPO_INJECT_SWEEP_STALL) h->inject = 0;
       if (e != cudaSuccess) return e;
     } else {
       note_launch(), k_coarse_gemv<<<dim3(cdiv((long long)pc.Nt * 32, 256), nsys), 256, 0, st>>>(pc.d_Kcinv, pc.d_rc, pc.d_uc, pc.Nt, sys0);

@@ -68,7 +68,7 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
            "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
            "mstopo_get_stats", "mstopo_apply_K_f32_noalloc", "mstopo_batch_build_preconditioner",
-           "mstopo_batch_solve", "mstopo_apply_K_f32_ex"]
+           "mstopo_batch_solve", "mstopo_apply_K_f32_ex", "mstopo_inject"]
 
 
 def load(path: str = LIB_PATH):
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "mstopo_batch_build_preconditioner": ([C.POINTER(vp), i32, i32, vp], i32),
         "mstopo_batch_solve": ([C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), vp], i32),
         "mstopo_apply_K_f32_ex": ([vp, i32, vp, vp, i32], i32),
+        "mstopo_inject": ([vp, i32], i32),
         "mstopo_apply_K_f32_noalloc": ([vp, vp, vp, vp, i32, i32, dbl, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -247,6 +248,10 @@ class Problem:
         self._check(_lib.mstopo_apply_K_f32_ex(self._h, realisation, _ptr(u), _ptr(y),
                                                1 if input_masked else 0))
         return y
+
+    def inject(self, what: int):
+        """Test injection (mstopo_inject): 1 = stall the next coarse block sweep's barrier."""
+        self._check(_lib.mstopo_inject(self._h, what))
 
     def apply_precond(self, r: torch.Tensor, precision: int = FP64, part: int = 0) -> torch.Tensor:
         r = _dev(r)

@@ -322,3 +322,90 @@ def test_periodic_26m_structure_on_a_reduced_copy_against_oracle():
     assert fr == pytest.approx(ref["f_robust"], rel=1e-9)
     g = g.cpu().numpy()
     assert np.linalg.norm(g - ref["dfdrho"]) <= 1e-7 * np.linalg.norm(ref["dfdrho"])
+
+
+def test_injected_sweep_stall_times_out_and_handle_recovers():
+    """A grid barrier of the coarse block sweeps that cannot complete (test injection) gives up
+    within its bound: the call returns TIMEOUT, nothing faults, and the next call works."""
+    m = _gpu()
+    wl = workloads.small(96, 48, seed=12, kind="random", H=4, n_eig=4, Emin=1e-3)
+    prob = make_problem(m, wl, coarse_solver="blocktri")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    r = torch.from_numpy(np.random.default_rng(5).standard_normal(prob.n_dof)).cuda()
+    z_ok = prob.apply_precond(r, m.FP64, 1).cpu().numpy()
+    prob.inject(1)
+    with pytest.raises(m.MstopoError) as ei:
+        prob.apply_precond(r, m.FP64, 1)
+    assert ei.value.status == 7   # MSTOPO_TIMEOUT
+    z_again = prob.apply_precond(r, m.FP64, 1).cpu().numpy()
+    assert np.array_equal(z_ok, z_again)
+
+
+def test_reused_preconditioner_on_a_new_design():
+    """reuse_preconditioner keeps the last build across set_design (basis re-use, Sec. 5.1):
+    the solve on the perturbed design still reaches the tolerance and matches sparse LU."""
+    m = _gpu()
+    wl = workloads.small(64, 32, seed=15, kind="voids", H=8, n_eig=6, etas=(0.3, 0.5, 0.7),
+                         rmin=2.0, beta=8.0)
+    prob = make_problem(m, wl, "mixed", tol=1e-10, reuse_preconditioner=True)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    prob.solve(cuda(wl.force), -1)
+    rho2 = np.clip(wl.rho + 0.05 * np.random.default_rng(1).standard_normal(wl.rho.shape), 0, 1)
+    prob.set_design(cuda(rho2), wl.rmin, wl.beta, wl.etas, wl.cell)
+    u, infos = prob.solve(cuda(wl.force), -1)
+    import copy
+    wl2 = copy.copy(wl)
+    wl2.rho = rho2
+    ref = pipeline.run(wl2, "direct", with_grad=False)
+    for k, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
+
+
+def test_eigenvalue_threshold_basis():
+    """lambda_thresh > 0 keeps only eigenvalues below it (Sec. 2.4, lambda_Omega), capped at
+    n_eig: the kept count varies over the agglomerates and the solve still matches sparse LU."""
+    m = _gpu()
+    wl = workloads.small(64, 32, seed=16, kind="voids", H=8, n_eig=8)
+    prob = make_problem(m, wl, "fp64", tol=1e-10, lambda_thresh=2e-3)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    info = prob.build_preconditioner()
+    assert info["n_coarse"] < info["n_agglomerates"] * wl.n_eig
+    u, infos = prob.solve(cuda(wl.force), -1)
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    assert infos[0]["status"] == 0
+    assert infos[0]["compliance"] == pytest.approx(ref["c"][0], rel=1e-9)
+
+
+def test_fp32_matvec_all_realisations_in_one_launch():
+    """apply_K_f32(realisation=-1, input_masked) is the flexible CG's launch: bit-identical to
+    one call per realisation on inputs that are zero at the Dirichlet DOFs."""
+    m = _gpu()
+    wl = workloads.small(40, 24, seed=18, kind="random", H=4, etas=(0.3, 0.5, 0.7))
+    prob = make_problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    free = torch.from_numpy(~np.asarray(wl.fixed, dtype=bool).reshape(-1)).cuda()
+    u = torch.randn(3, prob.n_dof, device="cuda", dtype=torch.float32) * free
+    y_all = prob.apply_K_f32(u, -1, input_masked=True)
+    for k in range(3):
+        assert torch.equal(y_all[k], prob.apply_K_f32(u[k].clone(), k))
+
+
+def test_invalid_calls_are_rejected():
+    m = _gpu()
+    wl33 = workloads.small(66, 66, seed=1, kind="solid", H=33)
+    with pytest.raises(m.MstopoError):   # H above 32 (the patch solve's row coverage)
+        m.Problem(66, 66, wl33.fixed, H=33, n_eig=4)
+    wl = workloads.small(32, 16, seed=19, kind="voids", H=8, n_eig=4)
+    prob = make_problem(m, wl)
+    with pytest.raises(m.MstopoError) as ei:
+        prob.solve(cuda(wl.force), -1)
+    assert ei.value.status == 8   # NOT_READY
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    with pytest.raises(m.MstopoError) as ei:
+        prob.apply_K_f32(torch.zeros(prob.n_dof, device="cuda"), 3)
+    assert ei.value.status == 1   # INVALID_ARG
+    with pytest.raises(m.MstopoError):
+        prob.inject(9)
