@@ -111,6 +111,10 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     return fail(MSTOPO_CUDA_ERROR);
   }
   if (getenv("MSTOPO_NO_GRAPHS")) h->graphs_enabled = 0;
+  if (getenv("MSTOPO_NO_FORK")) {   // run the preconditioner's coarse chain on the main stream
+    cudaStreamDestroy(h->s_side);
+    h->s_side = nullptr;
+  }
   h->nelx = d->nelx;
   h->nely = d->nely;
   h->n_nodes = (long long)(d->nelx + 1) * (d->nely + 1);
