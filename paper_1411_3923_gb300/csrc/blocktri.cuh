@@ -16,7 +16,8 @@
 // ------------------------------------------------------------------- factorisation (FP64)
 // S (nb x nb, global or shared) := lower Cholesky factor of S, in place.  Returns 0 on
 // success, or 1 + the failing pivot index.  Whole CTA participates.
-__device__ inline int bt_chol_inplace(double* S, int nb, int* sh_fail) {
+__device__ inline int bt_chol_inplace(double* S, int nb, int* sh_fail, double* dinv) {
+  __shared__ double sh_inv;
   if (threadIdx.x == 0) *sh_fail = 0;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
@@ -26,10 +27,13 @@ __device__ inline int bt_chol_inplace(double* S, int nb, int* sh_fail) {
         if (*sh_fail == 0) *sh_fail = 1 + j;
         d = 1.0;
       }
-      S[j * nb + j] = sqrt(d);
+      const double l = sqrt(d);
+      S[j * nb + j] = l;
+      sh_inv = 1.0 / l;             // one FP64 division per pivot, not one per thread
+      dinv[j] = sh_inv;
     }
     __syncthreads();
-    const double inv = 1.0 / S[j * nb + j];
+    const double inv = sh_inv;
     for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) S[i * nb + j] *= inv;
     __syncthreads();
     // trailing update of the lower triangle: S[i][l] -= S[i][j] S[l][j], j < l <= i
@@ -43,14 +47,15 @@ __device__ inline int bt_chol_inplace(double* S, int nb, int* sh_fail) {
   return *sh_fail;
 }
 
-// Linv := L^-1 for lower-triangular L (upper part of Linv set to 0).  One thread per column.
-__device__ inline void bt_tri_inverse(const double* L, double* Linv, int nb) {
+// Linv := L^-1 for lower-triangular L (upper part of Linv set to 0), dinv[i] = 1 / L[i][i].
+// One thread per column.
+__device__ inline void bt_tri_inverse(const double* L, const double* dinv, double* Linv, int nb) {
   for (int c = threadIdx.x; c < nb; c += blockDim.x) {
     for (int i = 0; i < c; ++i) Linv[i * nb + c] = 0.0;
     for (int i = c; i < nb; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int l = c; l < i; ++l) s = fma(-L[i * nb + l], Linv[l * nb + c], s);
-      Linv[i * nb + c] = s / L[i * nb + i];
+      Linv[i * nb + c] = s * dinv[i];
     }
   }
   __syncthreads();
@@ -62,7 +67,7 @@ __device__ inline void bt_tri_inverse(const double* L, double* Linv, int nb) {
 // Returns 0 or 1 + (global row index) of the first non-positive pivot.
 __device__ inline int bt_factor(const double* A, const double* B, const uint8_t* free,
                                 double shift, int nb, int NL, double* Linv, double* C,
-                                double* S, int* sh_fail) {
+                                double* S, int* sh_fail, double* dinv) {
   const int nn = nb * nb;
   int fail = 0;
   for (int k = 0; k < NL; ++k) {
@@ -81,10 +86,10 @@ __device__ inline int bt_factor(const double* A, const double* B, const uint8_t*
       S[t] = v;
     }
     __syncthreads();
-    int f = bt_chol_inplace(S, nb, sh_fail);
+    int f = bt_chol_inplace(S, nb, sh_fail, dinv);
     if (f && !fail) fail = k * nb + f;
     double* Li = Linv + (long long)k * nn;
-    bt_tri_inverse(S, Li, nb);
+    bt_tri_inverse(S, dinv, Li, nb);
     if (k + 1 < NL) {
       // C_k = B_k L_k^-T :  C[i][j] = sum_{l <= j} B[i][l] Linv[j][l]
       const double* Bk = B + (long long)k * nn;

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
                                                     double* __restrict__ Ld, int row_base,
                                                     int* __restrict__ status) {
   __shared__ double D[CB_TILE][CB_TILE + 1];
+  __shared__ double dinv[CB_TILE];   // 1 / L_jj, one FP64 division per pivot
   __shared__ int fail;
   const int c0 = p * CB_TILE, bs = min(CB_TILE, nb - c0);
   for (int t = threadIdx.x; t < CB_TILE * CB_TILE; t += blockDim.x) {
@@ -125,10 +126,12 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
         if (!fail) fail = 1 + j;
         d = 1.0;
       }
-      D[j][j] = sqrt(d);
+      const double l = sqrt(d);
+      D[j][j] = l;
+      dinv[j] = 1.0 / l;
     }
     __syncthreads();
-    const double inv = 1.0 / D[j][j];
+    const double inv = dinv[j];
     if ((int)threadIdx.x > j && (int)threadIdx.x < bs) D[threadIdx.x][j] *= inv;
     __syncthreads();
     for (int t = threadIdx.x; t < CB_TILE * CB_TILE; t += blockDim.x) {
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
     double sv = lane < bs ? row[lane] : 0.0;
     double x = 0.0;
     for (int j = 0; j < bs; ++j) {     // x L_pp^T = s, column by column
-      const double xj = __shfl_sync(0xffffffffu, sv / D[j][j], j);
+      const double xj = __shfl_sync(0xffffffffu, sv * dinv[j], j);
       if (lane == j) x = xj;
       if (lane > j) sv = fma(-xj, D[lane][j], sv);
     }
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(128) k_tri_inv(const double* __restrict__ S,
                                                  double* __restrict__ LinvT) {
   extern __shared__ double X[];                 // [nb - rbase][TI_W]
   __shared__ double Lb[CB_TILE][CB_TILE + 1];
+  __shared__ double Lbi[CB_TILE];   // 1 / Lb[i][i]
   __shared__ double Rs[CB_TILE][TI_W];
   const int c0 = blockIdx.x * TI_W;
   const int cw = min(TI_W, nb - c0);
@@ -195,12 +199,16 @@ __global__ void __launch_bounds__(128) k_tri_inv(const double* __restrict__ S,
       const int i = t / CB_TILE, l = t % CB_TILE;
       Lb[i][l] = (i < rb && l < rb) ? Dq[t] : (i == l ? 1.0 : 0.0);
     }
+    if (threadIdx.x < CB_TILE) {
+      const int i = threadIdx.x;
+      Lbi[i] = 1.0 / ((i < rb) ? Dq[i * CB_TILE + i] : 1.0);
+    }
     __syncthreads();
     {
       const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;   // warp j solves column j
       double sv = Rs[lane][j], x = 0.0;
       for (int m = 0; m < rb; ++m) {
-        const double xm = __shfl_sync(0xffffffffu, sv / Lb[m][m], m);
+        const double xm = __shfl_sync(0xffffffffu, sv * Lbi[m], m);
         if (lane == m) x = xm;
         if (lane > m) sv = fma(-xm, Lb[lane][m], sv);
       }

@@ -162,18 +162,20 @@ __global__ void k_assemble_box(const double* __restrict__ E, const uint8_t* __re
 
 // ------------------------------------------------------------------------ factorisation
 // systems [0, split) are factorised with diagonal shift s_lo, the others with s_hi
+#define BT_MAX_NB 1024   // largest block the one-CTA factor handles (inverse diagonal in shared memory)
 __global__ void k_bt_factor(const double* __restrict__ A, const double* __restrict__ B,
                             const uint8_t* __restrict__ freem, double s_lo, double s_hi,
                             int split, int nb, int NL, double* __restrict__ Linv,
                             double* __restrict__ C, double* __restrict__ Swork,
                             int* __restrict__ status) {
   __shared__ int sh_fail;
+  __shared__ double dinv[BT_MAX_NB];
   const long long nn = (long long)nb * nb;
   const int sys = blockIdx.x;
   const double shift = sys < split ? s_lo : s_hi;
   int f = bt_factor(A + sys * NL * nn, B + sys * (NL - 1) * nn,
                     freem ? freem + (long long)sys * NL * nb : nullptr, shift, nb, NL,
-                    Linv + sys * NL * nn, C + sys * (NL - 1) * nn, Swork + sys * nn, &sh_fail);
+                    Linv + sys * NL * nn, C + sys * (NL - 1) * nn, Swork + sys * nn, &sh_fail, dinv);
   if (threadIdx.x == 0) status[sys] = f;
 }
 
@@ -542,20 +544,115 @@ __device__ __forceinline__ void coarse_line_pos(const CoarseMap& m, int I, int J
   if (m.by_columns) { line = I; pos = J; } else { line = J; pos = I; }
 }
 
-__device__ __forceinline__ double hat(int x, int c, int H) {
-  double d = fabs((double)(x - c)) / H;
-  return d < 1.0 ? 1.0 - d : 0.0;
+// K_c = R_c K R_c^T element by element, organised by coarse cells: every element of cell
+// (cx, cy) lies in the boxes of exactly four agglomerates a = (cx + (a&1), cy + (a>>1)), so
+// per cell the ten blocks sum_e E_e phi_a,e^T K0 phi_b,e (a <= b) are formed from the four
+// phi_a,e = chi_a psi_a once per element (k_coarse_cell), and each block of K_c is then the
+// sum of the partials of the 1, 2 or 4 cells its two agglomerates share, in a fixed order
+// (k_coarse_gather).  chi_a = (H - |x - IH|)(H - |y - JH|) / H^2 (integer numerators).
+#define CC_CHUNK 16                   // elements of a cell staged together
+#define CC_OUT 10                     // pair-block outputs per thread (10 x 16^2 / 256)
+__device__ __forceinline__ int cc_pair(int a, int b) {   // a <= b in 0..3 -> 0..9
+  return a * 4 - a * (a - 1) / 2 + (b - a);
 }
 
-__global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
-    const double* __restrict__ E, int nelx, int nely, int H, const int* __restrict__ type_of,
-    const int* __restrict__ kept, const double* __restrict__ psi, int kmax, K0P K0, CoarseMap cm,
-    double* __restrict__ Ac, double* __restrict__ Bc, int nbc) {
-  // blockIdx.x = agglomerate i, blockIdx.y = neighbour (dI, dJ) in [-1,1]^2.
-  // Thread = (element lane, column b of agglomerate 2); kp columns per lane (kmax rounded up
-  // to 4, 8 or 16), 256 / kp element lanes.
-  __shared__ double red[PC_THREADS][MSTOPO_MAX_EIG + 1];
-  const int ncx = cm.ncx, ncy = cm.ncy;
+__global__ void __launch_bounds__(PC_THREADS) k_coarse_cell(
+    const double* __restrict__ E, int nelx, int nely, int H, int ncx,
+    const int* __restrict__ type_of, const int* __restrict__ kept,
+    const double* __restrict__ psi, int kmax, K0P K0, double* __restrict__ part) {
+  // part: [cell][10][kmax][kmax], block (a, b) row index over agglomerate a's basis
+  extern __shared__ double ccs[];
+  double* phi = ccs;                                   // [CHUNK][4][8][kmax]
+  double* G = phi + CC_CHUNK * 4 * 8 * kmax;           // [CHUNK][4][8][kmax] = E K0 phi
+  const int cell = blockIdx.x;
+  const int cx = cell % ncx, cy = cell / ncx;
+  const int N = 2 * H + 1;
+  const long long nbox = (long long)N * N * 2;
+  int Ia[4], Ja[4], ka[4];
+  const double* Pa[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    Ia[a] = cx + (a & 1);
+    Ja[a] = cy + (a >> 1);
+    const int i = Ja[a] * (ncx + 1) + Ia[a];
+    const int t = type_of[i];
+    ka[a] = kept[t];
+    Pa[a] = psi + (long long)t * nbox * kmax;
+  }
+  const double invH2 = 1.0 / (double)(H * H);
+  const int kk = kmax * kmax;
+  // output slots: 10 pairs x kmax x kmax, several per thread
+  const int nout = 10 * kk;
+  double acc[CC_OUT];
+  for (int q = 0; q < CC_OUT; ++q) acc[q] = 0.0;
+  for (int e0 = 0; e0 < H * H; e0 += CC_CHUNK) {
+    __syncthreads();
+    // phi of the chunk: (element, agglomerate, dof, column)
+    for (int t = threadIdx.x; t < CC_CHUNK * 4 * 8 * kmax; t += blockDim.x) {
+      const int col = t % kmax, dof = (t / kmax) % 8, a = (t / (8 * kmax)) % 4, le = t / (32 * kmax);
+      const int el = e0 + le;
+      const int ex = cx * H + el % H, ey = cy * H + el / H;
+      const int ln = dof >> 1, comp = dof & 1;
+      const int nx = ex + ((ln == 1 || ln == 2) ? 1 : 0), ny = ey + (ln >= 2 ? 1 : 0);
+      const int hx = max(H - abs(nx - Ia[a] * H), 0), hy = max(H - abs(ny - Ja[a] * H), 0);
+      const long long l = (long long)(ny - (Ja[a] - 1) * H) * N + (nx - (Ia[a] - 1) * H);
+      double v = 0.0;
+      if (el < H * H && col < ka[a] && hx > 0 && hy > 0)
+        v = (double)(hx * hy) * invH2 * Pa[a][(l * 2 + comp) * kmax + col];
+      phi[t] = v;
+    }
+    __syncthreads();
+    // G = E_e K0 phi  (per element, agglomerate and column: 8 outputs)
+    for (int t = threadIdx.x; t < CC_CHUNK * 4 * kmax; t += blockDim.x) {
+      const int col = t % kmax, a = (t / kmax) % 4, le = t / (4 * kmax);
+      const int el = e0 + le;
+      const int ex = cx * H + el % H, ey = cy * H + el / H;
+      const double Ee = el < H * H ? E[(long long)ey * nelx + ex] : 0.0;
+      const double* f = phi + ((le * 4 + a) * 8) * kmax + col;
+      double fv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) fv[c] = f[c * kmax];
+      double* g = G + ((le * 4 + a) * 8) * kmax + col;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        double sdot = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sdot = fma(K0.k[r * 8 + c], fv[c], sdot);
+        g[r * kmax] = Ee * sdot;
+      }
+    }
+    __syncthreads();
+    // pair blocks: out(p, i, j) += sum_e sum_r phi[e][a][r][i] G[e][b][r][j]
+    for (int q = 0; q < CC_OUT; ++q) {
+      const int o = threadIdx.x + q * blockDim.x;
+      if (o >= nout) break;
+      const int pr = o / kk, ij = o % kk, i = ij / kmax, j = ij % kmax;
+      int a = 0, b = 0;
+      for (int aa = 0, cnt = 0; aa < 4; ++aa)
+        for (int bb = aa; bb < 4; ++bb, ++cnt)
+          if (cnt == pr) { a = aa; b = bb; }
+      double sum = acc[q];
+      for (int le = 0; le < CC_CHUNK; ++le) {
+        const double* pa = phi + ((le * 4 + a) * 8) * kmax + i;
+        const double* gb = G + ((le * 4 + b) * 8) * kmax + j;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sum = fma(pa[r * kmax], gb[r * kmax], sum);
+      }
+      acc[q] = sum;
+    }
+  }
+  for (int q = 0; q < CC_OUT; ++q) {
+    const int o = threadIdx.x + q * blockDim.x;
+    if (o < nout) part[(long long)cell * nout + o] = acc[q];
+  }
+}
+
+// Block (i, i2) of K_c from the cell partials (grid: agglomerate i x 9 neighbours); the
+// storage and the padding rules are those of the line-blocked factor.
+__global__ void __launch_bounds__(PC_THREADS) k_coarse_gather(
+    const double* __restrict__ part, int ncx, int ncy, const int* __restrict__ type_of,
+    const int* __restrict__ kept, int kmax, CoarseMap cm, double* __restrict__ Ac,
+    double* __restrict__ Bc, int nbc) {
   const int i = blockIdx.x;
   const int I = i % (ncx + 1), J = i / (ncx + 1);
   const int I2 = I + (int)blockIdx.y % 3 - 1, J2 = J + (int)blockIdx.y / 3 - 1;
@@ -565,72 +662,27 @@ __global__ void __launch_bounds__(PC_THREADS) k_coarse_assemble(
   coarse_line_pos(cm, I2, J2, L2, P2);
   if (L2 == L1 - 1) return;   // stored through the transpose (block of line L2)
   const int i2 = J2 * (ncx + 1) + I2;
-  const int t1 = type_of[i], t2 = type_of[i2];
-  const int k1 = kept[t1], k2 = kept[t2];
-  const int N = 2 * H + 1;
-  const long long n = (long long)N * N * 2;
-  const double* P1s = psi + (long long)t1 * n * kmax;
-  const double* P2s = psi + (long long)t2 * n * kmax;
-  // element overlap of the two agglomerates, inside the mesh
-  const int x0 = max(max((I - 1) * H, (I2 - 1) * H), 0), x1 = min(min((I + 1) * H, (I2 + 1) * H), nelx);
-  const int y0 = max(max((J - 1) * H, (J2 - 1) * H), 0), y1 = min(min((J + 1) * H, (J2 + 1) * H), nely);
-  const int kp = kmax <= 4 ? 4 : (kmax <= 8 ? 8 : 16);
-  const int lanes = PC_THREADS / kp;
-  const int b = threadIdx.x % kp, lane = threadIdx.x / kp;
-  const double invH2 = 1.0 / (double)(H * H);
-  double acc[MSTOPO_MAX_EIG];
-  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) acc[a] = 0.0;
-  const int nex = x1 - x0, ney = y1 - y0;
-  if (b < k2 && nex > 0 && ney > 0) {
-    for (int e = lane; e < nex * ney; e += lanes) {
-      const int ex = x0 + e % nex, ey = y0 + e / nex;
-      const double Ee = E[(long long)ey * nelx + ex];
-      double f2[8];                   // phi_2 (column b) at the element DOFs
-      double c1[4];                   // chi_1 at the element nodes
-      long long l1[4];                // node index in agglomerate 1's box
-#pragma unroll
-      for (int ln = 0; ln < 4; ++ln) {
-        const int nx = ex + ((ln == 1 || ln == 2) ? 1 : 0), ny = ey + (ln >= 2 ? 1 : 0);
-        // bilinear hats with integer numerators (H - |x - IH|)(H - |y - JH|) / H^2
-        const int h1x = max(H - abs(nx - I * H), 0), h1y = max(H - abs(ny - J * H), 0);
-        const int h2x = max(H - abs(nx - I2 * H), 0), h2y = max(H - abs(ny - J2 * H), 0);
-        c1[ln] = (double)(h1x * h1y) * invH2;
-        const double c2 = (double)(h2x * h2y) * invH2;
-        l1[ln] = (long long)(ny - (J - 1) * H) * N + (nx - (I - 1) * H);
-        const long long l2 = (long long)(ny - (J2 - 1) * H) * N + (nx - (I2 - 1) * H);
-        f2[2 * ln] = c2 * P2s[(l2 * 2) * kmax + b];
-        f2[2 * ln + 1] = c2 * P2s[(l2 * 2 + 1) * kmax + b];
-      }
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        if (c1[rr >> 1] == 0.0) continue;
-        double sdot = 0.0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) sdot = fma(K0.k[rr * 8 + c], f2[c], sdot);
-        const double w = Ee * sdot * c1[rr >> 1];
-        const double* p1 = P1s + (l1[rr >> 1] * 2 + (rr & 1)) * kmax;
-#pragma unroll
-        for (int a = 0; a < MSTOPO_MAX_EIG; ++a)
-          if (a < k1) acc[a] = fma(w, p1[a], acc[a]);
+  const int k1 = kept[type_of[i]], k2 = kept[type_of[i2]];
+  const int kk = kmax * kmax;
+  for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+    const int aa = t / kmax, bb = t % kmax;   // row basis index (agglomerate i), column (i2)
+    double s = 0.0;
+    // cells shared by the two boxes: cx in {I-1, I} and {I2-1, I2}, inside the mesh
+    for (int cy = max(J, J2) - 1; cy <= min(J, J2); ++cy) {
+      if (cy < 0 || cy >= ncy) continue;
+      for (int cx = max(I, I2) - 1; cx <= min(I, I2); ++cx) {
+        if (cx < 0 || cx >= ncx) continue;
+        const int a = (I - cx) + 2 * (J - cy), b = (I2 - cx) + 2 * (J2 - cy);
+        const double* pc = part + ((long long)(cy * ncx + cx) * 10) * kk;
+        s += (a <= b) ? pc[cc_pair(a, b) * kk + aa * kmax + bb] : pc[cc_pair(b, a) * kk + bb * kmax + aa];
       }
     }
-  }
-  for (int a = 0; a < MSTOPO_MAX_EIG; ++a) red[threadIdx.x][a] = acc[a];
-  __syncthreads();
-  // reduce over lanes in fixed order and write the block
-  const int nn = nbc;
-  for (int t = threadIdx.x; t < MSTOPO_MAX_EIG * MSTOPO_MAX_EIG; t += blockDim.x) {
-    const int bb = t / MSTOPO_MAX_EIG, aa = t % MSTOPO_MAX_EIG;
-    if (aa >= kmax || bb >= kmax) continue;
-    double s = 0.0;
-    if (bb < kp)
-      for (int l = 0; l < lanes; ++l) s += red[l * kp + bb][aa];
     const int row_slot = P1 * kmax + aa, col_slot = P2 * kmax + bb;
     double v;
     if (aa < k1 && bb < k2) v = s;
     else v = (i == i2 && aa == bb) ? 1.0 : 0.0;   // padding slots: identity
-    if (L2 == L1) Ac[((long long)L1 * nn + row_slot) * nn + col_slot] = v;
-    else Bc[((long long)L1 * nn + col_slot) * nn + row_slot] = v;   // B_L1 = A(L1+1, L1)
+    if (L2 == L1) Ac[((long long)L1 * nbc + row_slot) * nbc + col_slot] = v;
+    else Bc[((long long)L1 * nbc + col_slot) * nbc + row_slot] = v;   // B_L1 = A(L1+1, L1)
   }
 }
 
@@ -1354,12 +1406,31 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMalloc(&cB, nsv * nlB * 8));
   CKB(cudaMemsetAsync(cA, 0, nsv * nlA * 8, s));
   CKB(cudaMemsetAsync(cB, 0, nsv * nlB * 8, s));
-  for (int k = 0; k < nsv; ++k) {   // K_c of realisation k on the shared basis
-    note_launch(), k_coarse_assemble<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(h->d_E64 + (long long)k * h->n_el,
-                                                            h->nelx, h->nely, H, pc.d_type_of_agg,
-                                                            pc.d_kept, pc.d_psi64, pc.kmax, K0, cm,
-                                                            cA + k * nlA, cB + k * nlB, nbc);
-    CKB(cudaGetLastError());
+  {
+    // K_c of every realisation on the shared basis: cell partials, then the blocks
+    const int ncell = pc.ncx * pc.ncy;
+    double* cpart;
+    CKB(cudaMalloc(&cpart, (size_t)ncell * 10 * pc.kmax * pc.kmax * 8));
+    const size_t ccs = (size_t)2 * CC_CHUNK * 4 * 8 * pc.kmax * 8;
+    if (10 * pc.kmax * pc.kmax > CC_OUT * PC_THREADS || ccs > 200 * 1024) {
+      cudaFree(cpart);
+      h->err = "n_eig too large for the coarse assembly";
+      return MSTOPO_INVALID_ARG;
+    }
+    CKB(smem_limit_max<k_coarse_cell>());
+    for (int k = 0; k < nsv; ++k) {
+      note_launch(), k_coarse_cell<<<ncell, PC_THREADS, ccs, s>>>(h->d_E64 + (long long)k * h->n_el,
+                                                                 h->nelx, h->nely, H, pc.ncx,
+                                                                 pc.d_type_of_agg, pc.d_kept,
+                                                                 pc.d_psi64, pc.kmax, K0, cpart);
+      CKB(cudaGetLastError());
+      note_launch(), k_coarse_gather<<<dim3(pc.Nc, 9), PC_THREADS, 0, s>>>(cpart, pc.ncx, pc.ncy,
+                                                              pc.d_type_of_agg, pc.d_kept, pc.kmax,
+                                                              cm, cA + k * nlA, cB + k * nlB, nbc);
+      CKB(cudaGetLastError());
+    }
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(cpart);
   }
   // slots beyond the mesh's coarse nodes do not exist (per_line covers them all)
   int mode = h->p.coarse_solver;
@@ -1369,6 +1440,11 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   pc.NLc = NLc;
   std::vector<int> cst(nsv, 0);
   CKB(cudaMemsetAsync(d_st, 0, nsv * sizeof(int), s));
+  if (mode == MSTOPO_COARSE_DENSE && nbc > 640) {
+    cudaFree(cA); cudaFree(cB); cudaFree(d_s2o);
+    h->err = "coarse line too long for the dense coarse solver (coarse nodes per line x n_eig > 640)";
+    return MSTOPO_INVALID_ARG;
+  }
   if (mode == MSTOPO_COARSE_DENSE) {
     // one-CTA block factor per realisation, then the explicit inverses by identity columns
     CKB(cudaMalloc(&cLi, nsv * nlA * 8));
