@@ -87,6 +87,11 @@ typedef struct {
                                 built (on an earlier design, with the same number of
                                 realisations) instead of requiring a new build -- the basis
                                 re-use of Sec. 5.1-5.2; solves still stop on the true residual */
+  double rebuild_ratio;      /* with reuse_preconditioner, > 0: the update rule of Sec. 5.2 --
+                                when an all-realisation solve needs more than rebuild_ratio x
+                                the iterations of the first solve after the last build, the
+                                next all-realisation solve first rebuilds the preconditioner on
+                                the design set then (0 = never rebuild automatically) */
 } mstopo_problem;
 
 typedef struct {
@@ -246,6 +251,9 @@ typedef struct {
   int64_t launches;            /* kernels launched by this library in this process so far    */
   int64_t kernel_launches[4];  /* profiled launches: [0] patch solves, [1] FP32 matvec,         */
   double kernel_ms[4];         /* [2] FP64 matvec, [3] coarse solve; device ms summed (events) */
+  int64_t builds;              /* preconditioner builds of this handle (explicit + automatic) */
+  int32_t base_iterations;     /* iterations of the first solve after the last build, or -1  */
+  int32_t rebuild_pending;     /* 1: the next all-realisation solve rebuilds first            */
 } mstopo_stats;
 
 /* Turn per-kernel event timing on (1) or off (0) for this handle; resets its counters.

@@ -1,6 +1,7 @@
 // C-ABI entry points of the mstopo library (declared in include/mstopo.h).
 // Host orchestration only: argument checks, workspace ownership, kernel sequencing on the
 // handle's stream.  Every step of the numerical path runs in the kernels of this library.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -86,7 +87,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
   bool ok = d->nelx > 0 && d->nely > 0 && d->H >= 2 && d->nelx % d->H == 0 && d->nely % d->H == 0 &&
             d->nelx / d->H >= 2 && d->nely / d->H >= 2 && d->n_eig >= 1 && d->n_eig <= MSTOPO_MAX_EIG &&
             d->nu >= 0.0 && d->nu < 0.5 && d->Emin > 0.0 && d->Emin <= d->E0 && d->fixed != nullptr &&
-            d->tol > 0.0 && d->max_iter > 0 && d->local_shift >= 0.0 &&
+            d->tol > 0.0 && d->max_iter > 0 && d->local_shift >= 0.0 && d->rebuild_ratio >= 0.0 &&
             (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 32 &&
             d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI;
   if (!ok) {
@@ -258,6 +259,9 @@ mstopo_status mstopo_build_preconditioner(mstopo_handle* h, int32_t ref, mstopo_
   CHECK_ARG(ref < h->n_eta, "reference realisation out of range");
   h->pc_ref = ref;
   h->pc_generation++;
+  h->builds++;
+  h->base_iters = -1;
+  h->rebuild_pending = 0;
   mstopo_status st = precond_build(h, ref, info);
   if (st != MSTOPO_OK) h->pc.built = 0;
   return st;
@@ -271,7 +275,20 @@ mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* 
   CHECK_ARG(realisation >= -1 && realisation < h->n_eta, "realisation out of range");
   const int sys0 = realisation < 0 ? 0 : realisation;
   const int nsys = realisation < 0 ? h->n_eta : 1;
-  mstopo_status st = fcg_solve(h, sys0, nsys, f, u, u0, infos);
+  const bool policy = realisation < 0 && h->p.reuse_preconditioner && h->p.rebuild_ratio > 0.0;
+  if (policy && h->rebuild_pending) {   // the update rule of Sec. 5.2: new basis for this design
+    mstopo_status sb = mstopo_build_preconditioner(h, -1, nullptr);
+    if (sb != MSTOPO_OK) return sb;
+  }
+  mstopo_solve_info local[MSTOPO_MAX_SYS];
+  mstopo_solve_info* inf = infos ? infos : local;
+  mstopo_status st = fcg_solve(h, sys0, nsys, f, u, u0, inf);
+  if (policy && st == MSTOPO_OK) {
+    int it = 0;
+    for (int k = 0; k < nsys; ++k) it = std::max(it, (int)inf[k].iterations);
+    if (h->base_iters < 0) h->base_iters = it;
+    else if (it > h->p.rebuild_ratio * h->base_iters) h->rebuild_pending = 1;
+  }
   if (realisation < 0) {
     CKA(cudaMemcpyAsync(h->d_u_all, u, (size_t)nsys * h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
     CKA(cudaMemcpyAsync(h->d_f_all, f, (size_t)h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
@@ -456,6 +473,9 @@ mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out) {
   CKA(cudaStreamSynchronize(h->s));
   prof_collect(h->prof);
   out->launches = g_launch_count.load();
+  out->builds = h->builds;
+  out->base_iterations = h->base_iters;
+  out->rebuild_pending = h->rebuild_pending;
   for (int k = 0; k < 4; ++k) {
     out->kernel_launches[k] = h->prof.n[k];
     out->kernel_ms[k] = h->prof.ms[k];

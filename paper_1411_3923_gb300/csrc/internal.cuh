@@ -211,6 +211,9 @@ struct mstopo_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs_enabled = 1;
   int inject = 0;                     // test injection (mstopo_inject), consumed by its target
+  long long builds = 0;               // preconditioner builds (explicit and automatic)
+  int base_iters = -1;                // iterations of the first solve after the last build
+  int rebuild_pending = 0;            // the update rule asked for a rebuild
   long long pc_generation = 0;        // bumped by every preconditioner build
   FcgGraph fcg_graph;
 };

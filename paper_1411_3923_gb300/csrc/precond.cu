@@ -341,7 +341,7 @@ __device__ void box_apply_cols(const EigArgs& a, int I, int J, const uint8_t* fr
   }
 }
 
-// One 4-CTA cluster per agglomerate type.  CTA rank r owns the subspace columns
+// One EIG_CL-CTA cluster per agglomerate type.  CTA rank r owns the subspace columns
 // [r*QC, (r+1)*QC): it applies the shifted inverse and K_w to them; the q x q projections
 // G = Y^T K Y, M = Y^T D Y are assembled from all columns (global memory, cluster barriers)
 // and every CTA performs the same small Rayleigh-Ritz step.
@@ -1236,8 +1236,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   const long long nnP = nnA, nP = nA;
   const int TP = T * nsv;             // patch operators
   const int NS = T + TP;              // factorised systems
-  // subspace dimension: 2k + 4 rounded up to a multiple of 4 (compile-time variants)
-  const int q = std::min(((2 * pc.kmax + 4) + 3) / 4 * 4, 2 * MSTOPO_MAX_EIG);
+  // subspace dimension: 2k + 4 rounded up to a multiple of the cluster size (compile-time variants)
+  const int q = std::min(((2 * pc.kmax + 4) + EIG_CL - 1) / EIG_CL * EIG_CL, 2 * MSTOPO_MAX_EIG);
   double *dA, *dB, *dLi, *dC, *dS, *dX, *dY, *dKY, *dKX, *dYsc, *dGM, *dres;
   uint8_t* dfree_;
   int* d_st;

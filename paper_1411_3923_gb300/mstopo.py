@@ -34,7 +34,8 @@ class _Problem(C.Structure):
                 ("H", C.c_int32), ("n_eig", C.c_int32), ("lambda_thresh", C.c_double),
                 ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("local_shift", C.c_double), ("stream", C.c_void_p),
-                ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32)]
+                ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32),
+                ("rebuild_ratio", C.c_double)]
 
 
 class _BuildInfo(C.Structure):
@@ -47,7 +48,8 @@ class _BuildInfo(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("kernel_launches", C.c_int64 * 4),
-                ("kernel_ms", C.c_double * 4)]
+                ("kernel_ms", C.c_double * 4), ("builds", C.c_int64),
+                ("base_iterations", C.c_int32), ("rebuild_pending", C.c_int32)]
 
 
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
@@ -137,7 +139,7 @@ class Problem:
                  n_eig: int = 4, lambda_thresh: float = 0.0, precision: str = "mixed",
                  tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
                  stream: Optional[int] = None, coarse_solver: str = "auto",
-                 reuse_preconditioner: bool = False):
+                 reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
@@ -145,7 +147,7 @@ class Problem:
         d = _Problem(nelx, nely, nu, E0, Emin, penal, self._fixed.ctypes.data, H, n_eig,
                      lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
                      local_shift, stream, COARSE_SOLVERS[coarse_solver],
-                     1 if reuse_preconditioner else 0)
+                     1 if reuse_preconditioner else 0, rebuild_ratio)
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:
@@ -269,7 +271,8 @@ class Problem:
 
 
 def _stats_dict(st: "_Stats") -> dict:
-    out = {"launches": st.launches}
+    out = {"launches": st.launches, "builds": st.builds, "base_iterations": st.base_iterations,
+           "rebuild_pending": st.rebuild_pending}
     for name, k in KERNEL_IDS.items():
         out[name] = {"launches": st.kernel_launches[k], "ms": st.kernel_ms[k]}
     return out

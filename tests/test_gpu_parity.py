@@ -409,3 +409,30 @@ def test_invalid_calls_are_rejected():
     assert ei.value.status == 1   # INVALID_ARG
     with pytest.raises(m.MstopoError):
         prob.inject(9)
+
+
+@pytest.mark.parametrize("ratio,rebuilds", [(0.5, True), (100.0, False)])
+def test_basis_update_rule(ratio, rebuilds):
+    """The update rule of Sec. 5.2 (reuse_preconditioner with rebuild_ratio): a solve that needs
+    more than ratio x the iterations of the first solve after the last build marks a rebuild,
+    which the next all-realisation solve performs first.  Ratio 0.5 triggers on an unchanged
+    design (same iteration count), ratio 100 never does; every solve still matches sparse LU."""
+    m = _gpu()
+    wl = workloads.small(64, 32, seed=21, kind="voids", H=8, n_eig=6, rmin=2.0, beta=8.0)
+    prob = make_problem(m, wl, "mixed", tol=1e-10, reuse_preconditioner=True, rebuild_ratio=ratio)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    f = cuda(wl.force)
+    _, i1 = prob.solve(f, -1)
+    st = prob.stats()
+    assert st["builds"] == 1 and st["base_iterations"] == i1[0]["iterations"]
+    assert st["rebuild_pending"] == 0
+    _, i2 = prob.solve(f, -1)
+    assert prob.stats()["rebuild_pending"] == (1 if rebuilds else 0)
+    _, i3 = prob.solve(f, -1)
+    st = prob.stats()
+    assert st["builds"] == (2 if rebuilds else 1)
+    for inf in i1 + i2 + i3:
+        assert inf["status"] == 0
+        assert inf["compliance"] == pytest.approx(ref["c"][0], rel=1e-9)
