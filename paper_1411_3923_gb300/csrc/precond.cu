@@ -179,12 +179,6 @@ __global__ void k_bt_factor(const double* __restrict__ A, const double* __restri
   if (threadIdx.x == 0) status[sys] = f;
 }
 
-__global__ void k_d2f_copy(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-
 // ------------------------------------------------------------------------------ eigen
 // Small dense helpers (thread 0 only).  Cyclic Jacobi for a symmetric q x q matrix:
 // on exit A is (numerically) diagonal and V holds the eigenvectors as columns.
