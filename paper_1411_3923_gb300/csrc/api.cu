@@ -112,6 +112,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     return fail(MSTOPO_CUDA_ERROR);
   }
   if (getenv("MSTOPO_NO_GRAPHS")) h->graphs_enabled = 0;
+  if (const char* v = getenv("MSTOPO_PATCH_TC")) h->patch_tc = atoi(v) != 0 ? 1 : 0;
   if (getenv("MSTOPO_NO_FORK")) {   // run the preconditioner's coarse chain on the main stream
     cudaStreamDestroy(h->s_side);
     h->s_side = nullptr;

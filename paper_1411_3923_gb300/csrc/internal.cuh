@@ -116,6 +116,19 @@ struct FcgGraph {              // one captured chunk of flexible-CG iterations
 
 // ---------------------------------------------------------------------------------------
 // Preconditioner (precond.cu)
+// Patch-solve work groups: per realisation k and type t, up to P agglomerates (one
+// right-hand-side column each); groups of realisation k are [h_begin[k], h_begin[k+1]).
+struct PatchGroups {
+  int* d_perm = nullptr;            // [nsv * Nc] agglomerates in group order
+  int* d_type = nullptr;            // [n] realisation * T + type
+  int* d_first = nullptr;           // [n] first entry of the group in d_perm
+  int* d_count = nullptr;           // [n] agglomerates in the group
+  int* d_sys = nullptr;             // [n] realisation
+  int* d_agg = nullptr;             // [2][nsv][Nc] group and column of each agglomerate
+  std::vector<int> h_begin;         // [nsv + 1]
+  int n = 0, P = 1;
+};
+
 struct Precond {
   int H = 0, NA = 0, NP = 0, nbA = 0, nbP = 0, ncx = 0, ncy = 0, Nc = 0, kmax = 0;
   int n_types = 0, Nt = 0;
@@ -125,13 +138,9 @@ struct Precond {
   int* d_type_of_agg = nullptr;     // [Nc]
   int* d_kept = nullptr;            // [n_types]
   int* d_coff = nullptr;            // [Nc+1] coarse-unknown offsets
-  int* d_perm = nullptr;            // [Nc] agglomerates sorted by type
-  int* d_grp_type = nullptr;        // [n_groups] patch-solve work items
-  int* d_grp_first = nullptr;
-  int* d_grp_count = nullptr;
-  int* d_grp_sys = nullptr;         // [n_groups] realisation of the group
-  std::vector<int> h_grp_begin;     // [nsv+1] first group of each realisation
-  int n_groups = 0;
+  // patch-solve work groups: [0] for the CUDA-core kernels (FP64, and FP32 when the tensor
+  // cores are off), [1] for the tensor-core FP32 kernel (PATCH_COLS patches per group)
+  PatchGroups pg[2];
   int nsv = 0;                      // realisations with their own operators
   // per-type patch factors (block tridiagonal by node rows of the (2H+1)^2 agglomerate box,
   // artificial-boundary nodes Dirichlet): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
@@ -141,7 +150,11 @@ struct Precond {
   // packed stage blocks for the cluster patch solve: [T][NL][4 ranks][2][rpc][nbs]
   double* d_pf64 = nullptr; double* d_pb64 = nullptr;
   float* d_pf32 = nullptr;  float* d_pb32 = nullptr;
-  int rpc = 0, nbs = 0, patches_per_group = 1;
+  int rpc = 0, nbs = 0;
+  // tensor-core FP32 patch solve (csrc/patch_tc.cu): TF32 hi/lo factor lines [T][2][NL][line]
+  unsigned char* d_ptc = nullptr;
+  long long tc_line_bytes = 0;
+  int patch_tc = 0;
   // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
   double* d_lambda = nullptr; double* d_psi64 = nullptr; float* d_psi32 = nullptr;
   double* d_eigres = nullptr;       // [T] residual norms
@@ -158,7 +171,6 @@ struct Precond {
   // apply buffers
   double* d_rc = nullptr;           // [MAX_SYS][Nt]
   double* d_uc = nullptr;           // [MAX_SYS][Nt]
-  double* d_rcpart = nullptr;       // restriction partials
   float* d_zp32 = nullptr;          // [MAX_SYS][Nc][NP*NP*2]
   double* d_zp64 = nullptr;
   // workspaces for the build
@@ -210,6 +222,7 @@ struct mstopo_handle {
   cudaStream_t s_side = nullptr;      // side stream of the preconditioner's coarse chain
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs_enabled = 1;
+  int patch_tc = -1;                  // FP32 patch solves on the tensor cores: -1 by problem size, 0 off, 1 on
   int inject = 0;                     // test injection (mstopo_inject), consumed by its target
   long long builds = 0;               // preconditioner builds (explicit and automatic)
   int base_iters = -1;                // iterations of the first solve after the last build
@@ -268,3 +281,10 @@ cudaError_t smem_limit_max() {
   }();
   return once;
 }
+
+// tensor-core FP32 patch solve (csrc/patch_tc.cu)
+long long patch_tc_line_bytes(int nb);
+size_t patch_tc_smem(int nb, int nst);
+cudaError_t patch_tc_pack(const double* Linv, const double* W, const double* V, int T, int nb,
+                          int NL, unsigned char* out, cudaStream_t s);
+cudaError_t patch_tc_solve(mstopo_handle* h, int Q, const float* r, int sys0, int nsys, float* Xg);

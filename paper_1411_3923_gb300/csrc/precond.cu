@@ -1131,8 +1131,8 @@ __global__ void k_patch_pack(const double* __restrict__ Linv, const double* __re
       else v = Mk[(long long)row * nb + c];
     }
     const long long o = (((long long)type * NL + k) * PATCH_HALVES) * blk + t;
-    if (bw) { b64[o] = v; b32[o] = (float)v; }
-    else { f64[o] = v; f32[o] = (float)v; }
+    if (bw) { b64[o] = v; if (b32) b32[o] = (float)v; }
+    else { f64[o] = v; if (f32) f32[o] = (float)v; }
   }
 }
 
@@ -1149,21 +1149,20 @@ __global__ void k_patch_pack(const double* __restrict__ Linv, const double* __re
 static void dfree(void* p) { if (p) cudaFree(p); }
 
 void precond_free(Precond& pc) {
-  dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff); dfree(pc.d_perm);
-  dfree(pc.d_grp_type); dfree(pc.d_grp_first); dfree(pc.d_grp_count); dfree(pc.d_grp_sys);
+  dfree(pc.d_type_of_agg); dfree(pc.d_kept); dfree(pc.d_coff);
+  for (PatchGroups& G : pc.pg) {
+    dfree(G.d_perm); dfree(G.d_type); dfree(G.d_first); dfree(G.d_count); dfree(G.d_sys); dfree(G.d_agg);
+  }
   dfree(pc.d_pfree); dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
-  dfree(pc.d_pf64); dfree(pc.d_pb64); dfree(pc.d_pf32); dfree(pc.d_pb32);
+  dfree(pc.d_pf64); dfree(pc.d_pb64); dfree(pc.d_pf32); dfree(pc.d_pb32); dfree(pc.d_ptc);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
   dfree(pc.d_Kc); dfree(pc.d_Kcinv);
   dfree(pc.d_cLinv); dfree(pc.d_cLinvT); dfree(pc.d_cW); dfree(pc.d_cV);
-  dfree(pc.d_cy); dfree(pc.d_cx); dfree(pc.d_s2o); dfree(pc.d_cbar); dfree(pc.d_rc); dfree(pc.d_uc); dfree(pc.d_rcpart);
+  dfree(pc.d_cy); dfree(pc.d_cx); dfree(pc.d_s2o); dfree(pc.d_cbar); dfree(pc.d_rc); dfree(pc.d_uc);
   dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
   pc = Precond();
 }
 
-// extra per-agglomerate maps for the combine kernel live behind d_rcpart (ints)
-static int* agg_group_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart); }
-static int* agg_slot_ptr(Precond& pc) { return reinterpret_cast<int*>(pc.d_rcpart) + (size_t)pc.nsv * pc.Nc; }
 
 mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) {
   Precond old = h->pc;
@@ -1354,8 +1353,19 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     const size_t pk = (size_t)TP * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
     CKB(cudaMalloc(&pc.d_pf64, pk * 8));
     CKB(cudaMalloc(&pc.d_pb64, pk * 8));
-    CKB(cudaMalloc(&pc.d_pf32, pk * 4));
-    CKB(cudaMalloc(&pc.d_pb32, pk * 4));
+    // FP32: the tensor-core line pack, or the CUDA-core stage blocks
+    // The tensor-core kernel's line has a fixed MMA chain (68 tcgen05.mma whatever the number
+    // of columns): it pays off with full 16-column groups and two CTAs per SM; on small
+    // problems (a few patches per SM) the CUDA-core kernel's shorter line wins.
+    pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 32LL * sms);
+    if (pc.patch_tc) {
+      pc.tc_line_bytes = patch_tc_line_bytes(nbP);
+      CKB(cudaMalloc(&pc.d_ptc, (size_t)TP * 2 * NP * pc.tc_line_bytes));
+      CKB(patch_tc_pack(pLi, dW, dV, TP, nbP, NP, pc.d_ptc, s));
+    } else {
+      CKB(cudaMalloc(&pc.d_pf32, pk * 4));
+      CKB(cudaMalloc(&pc.d_pb32, pk * 4));
+    }
     note_launch(), k_patch_pack<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, dW, dV, nbP, NP, pc.rpc,
                                                                     pc.nbs, pc.d_pf64, pc.d_pb64,
                                                                     pc.d_pf32, pc.d_pb32);
@@ -1502,47 +1512,45 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   //    on large ones.
   std::vector<std::vector<int>> by_type(T);
   for (int i = 0; i < pc.Nc; ++i) by_type[pc.h_type_of_agg[i]].push_back(i);
-  std::vector<int> perm, gt, gf, gc, gs, agg_group((size_t)nsv * pc.Nc), agg_slot((size_t)nsv * pc.Nc);
-  pc.patches_per_group = P;
-  pc.h_grp_begin.assign(nsv + 1, 0);
-  for (int k = 0; k < nsv; ++k) {
-    pc.h_grp_begin[k] = (int)gt.size();
-    for (int t = 0; t < T; ++t)
-      for (size_t b = 0; b < by_type[t].size(); b += P) {
-        int g = (int)gt.size();
-        gt.push_back(k * T + t);
-        gs.push_back(k);
-        gf.push_back((int)perm.size());
-        int c = (int)std::min<size_t>(P, by_type[t].size() - b);
-        gc.push_back(c);
-        for (int p = 0; p < c; ++p) {
-          int i = by_type[t][b + p];
-          agg_group[(size_t)k * pc.Nc + i] = g;
-          agg_slot[(size_t)k * pc.Nc + i] = p;
-          perm.push_back(i);
+  auto build_groups = [&](PatchGroups& G, int Pg) -> cudaError_t {
+    std::vector<int> perm, gt, gf, gc, gs, agg((size_t)2 * nsv * pc.Nc);
+    G.P = Pg;
+    G.h_begin.assign(nsv + 1, 0);
+    for (int k = 0; k < nsv; ++k) {
+      G.h_begin[k] = (int)gt.size();
+      for (int t = 0; t < T; ++t)
+        for (size_t b = 0; b < by_type[t].size(); b += Pg) {
+          const int g = (int)gt.size();
+          gt.push_back(k * T + t);
+          gs.push_back(k);
+          gf.push_back((int)perm.size());
+          const int c = (int)std::min<size_t>(Pg, by_type[t].size() - b);
+          gc.push_back(c);
+          for (int p = 0; p < c; ++p) {
+            const int i = by_type[t][b + p];
+            agg[(size_t)k * pc.Nc + i] = g;
+            agg[((size_t)nsv + k) * pc.Nc + i] = p;
+            perm.push_back(i);
+          }
         }
-      }
-  }
-  pc.h_grp_begin[nsv] = (int)gt.size();
-  pc.n_groups = (int)gt.size();
-  CKB(cudaMalloc(&pc.d_perm, perm.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_grp_type, gt.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_grp_first, gf.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_grp_count, gc.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_grp_sys, gs.size() * sizeof(int)));
-  CKB(cudaMalloc(&pc.d_rcpart, (size_t)2 * nsv * pc.Nc * sizeof(int)));
-  CKB(cudaMemcpyAsync(pc.d_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(pc.d_grp_type, gt.data(), gt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(pc.d_grp_first, gf.data(), gf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(pc.d_grp_count, gc.data(), gc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(pc.d_grp_sys, gs.data(), gs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(agg_group_ptr(pc), agg_group.data(), agg_group.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(agg_slot_ptr(pc), agg_slot.data(), agg_slot.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  // the host copies above read vectors that go out of scope: wait for them
+    }
+    G.h_begin[nsv] = (int)gt.size();
+    G.n = (int)gt.size();
+    cudaError_t e = cudaSuccess;
+    auto up = [&](int*& d, const std::vector<int>& v) {
+      if (e == cudaSuccess) e = cudaMalloc(&d, v.size() * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+    };
+    up(G.d_perm, perm); up(G.d_type, gt); up(G.d_first, gf); up(G.d_count, gc); up(G.d_sys, gs);
+    up(G.d_agg, agg);
+    return e;
+  };
   CKB(cudaStreamSynchronize(s));
+  CKB(build_groups(pc.pg[0], P));
+  if (pc.patch_tc) CKB(build_groups(pc.pg[1], PATCH_COLS));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
-  const size_t xg = (size_t)pc.n_groups * nP * PATCH_COLS;
+  const size_t xg = (size_t)std::max(pc.pg[0].n, pc.pg[1].n) * nP * PATCH_COLS;
   CKB(cudaMalloc(&pc.d_zp32, xg * 4));
   CKB(cudaMalloc(&pc.d_zp64, xg * 8));
   CKB(cudaEventRecord(ev[5], s));
@@ -1587,10 +1595,11 @@ static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys
     if (e != cudaSuccess) return e;
   }
   if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
-  const int g0 = pc.h_grp_begin[sys0], ng = pc.h_grp_begin[sys0 + nsys] - g0;
+  const PatchGroups& G = pc.pg[0];
+  const int g0 = G.h_begin[sys0], ng = G.h_begin[sys0 + nsys] - g0;
   note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, patch_threads(Q) * patch_cg(Q), sm, h->s>>>(
-      r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, pc.d_grp_type, pc.d_grp_sys,
-      pc.d_grp_first, pc.d_grp_count, pc.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
+      r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, G.d_type, G.d_sys,
+      G.d_first, G.d_count, G.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
       h->d_flag + 1);
   return cudaGetLastError();
 }
@@ -1641,13 +1650,18 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
     cudaError_t e = cudaEventRecord(h->ev_join, sc);
     if (e != cudaSuccess) return e;
   }
+  bool use_tc = false;
+  if constexpr (sizeof(T) == 4) use_tc = pc.patch_tc != 0;
+  const PatchGroups& G = pc.pg[use_tc ? 1 : 0];
   int Rcols = 4;
   if (part != 1) {
-    const int Q = (pc.patches_per_group + 3) / 4;
+    const int Q = (G.P + 3) / 4;
     Rcols = 4 * Q;
     cudaEvent_t pa = prof_begin(h->prof, s);
     cudaError_t e;
-    switch (Q) {
+    if (use_tc) {
+      if constexpr (sizeof(T) == 4) e = patch_tc_solve(h, Q, r, sys0, nsys, Xg);
+    } else switch (Q) {
       case 1: e = launch_patch<T, 1>(h, r, sys0, nsys, fwd, bwd, Xg); break;
       case 2: e = launch_patch<T, 2>(h, r, sys0, nsys, fwd, bwd, Xg); break;
       case 3: e = launch_patch<T, 3>(h, r, sys0, nsys, fwd, bwd, Xg); break;
@@ -1666,7 +1680,7 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
   }
   note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, sys0, pc.Nc, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
-                                               pc.d_uc, pc.Nt, agg_group_ptr(pc), agg_slot_ptr(pc), Xg,
+                                               pc.d_uc, pc.Nt, G.d_agg, G.d_agg + (size_t)pc.nsv * pc.Nc, Xg,
                                                Rcols, h->d_nmask, part);
   return cudaGetLastError();
 }

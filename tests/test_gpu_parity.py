@@ -96,6 +96,39 @@ def test_patch_solves_match_sparse_lu():
     assert np.linalg.norm(z32 - z_ref) <= 1e-2 * np.linalg.norm(z_ref)
 
 
+@pytest.mark.parametrize("size,H,etas", [
+    ((128, 64), 32, (0.5,)),             # nb = 130: factor rows 128, 129 on the CUDA cores
+    ((40, 24), 4, (0.5,)),               # 4 columns per CTA, one patch each
+    ((60, 40), 2, (0.5,)),               # 8 columns
+    ((80, 64), 2, (0.5,)),               # 12 columns
+    ((128, 128), 2, (0.5,)),             # 16 columns
+    ((1024, 768), 32, (0.3, 0.5, 0.7)),  # 16 columns of 130-row lines, three realisations
+])
+def test_tensor_core_patch_solves(monkeypatch, size, H, etas):
+    """The FP32 patch solves on the tensor cores against the FP64 patch solves of the same
+    factors (Sec. 3.2), next to the FP32 CUDA-core solves.  A TF32 pair (high + low part)
+    carries 22 significant bits where FP32 carries 24, for the factor and for the vectors, so
+    the bound is the FP32 error scaled by that representation (4x each) plus 2^-22-relative
+    slack; both must stay far below the preconditioner's own approximation error."""
+    m = _gpu()
+    wl = workloads.small(*size, seed=21, kind="voids", H=H, n_eig=4, etas=etas, Emin=1e-3)
+    rng = np.random.default_rng(5)
+    r = cuda(rng.standard_normal((wl.nely + 1, wl.nelx + 1, 2)))
+    err = {}
+    for tc in ("1", "0"):
+        monkeypatch.setenv("MSTOPO_PATCH_TC", tc)
+        prob = make_problem(m, wl, precision="mixed")
+        prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+        prob.build_preconditioner()
+        z64 = prob.apply_precond(r, m.FP64, 2)
+        z32 = prob.apply_precond(r, m.MIXED, 2)
+        assert torch.isfinite(z32).all()
+        err[tc] = (torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)).item()
+        del prob
+    assert err["1"] < 1e-5, err
+    assert err["1"] <= 16.0 * err["0"] + 2.0 ** -22, err
+
+
 def test_eigenpairs_satisfy_generalised_eigenproblem():
     """Every kept pair satisfies K_w psi = lambda diag(K_w) psi (Sec. 2.4, 3.2) with the
     oracle's assembled agglomerate matrix, and the eigenvalues match the oracle's."""
@@ -234,6 +267,30 @@ def test_solve_with_blocktri_coarse_solver(precision):
     prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
     info = prob.build_preconditioner()
     assert info["coarse_solver"] == 2 and info["coarse_line"] == 42
+    u, infos = prob.solve(cuda(wl.force), -1)
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    grid, K0, oprob, _ = pipeline.build(wl)
+    for k, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        Kf = oprob.free_matrix(ref["E"][k])
+        ug = grid.nodal_from_neutral(u[k].cpu().numpy())[oprob.free]
+        ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
+        assert msfem.energy_error(Kf, ur, ug) < 1e-6
+        assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
+
+
+@pytest.mark.parametrize("H", [8, 32])
+def test_mixed_solve_with_tensor_core_patches(monkeypatch, H):
+    """The mixed flexible CG with its FP32 patch solves forced onto the tensor cores (H = 32:
+    130-row lines, factor rows 128 and 129 on the CUDA cores) converges to the same solution
+    as sparse LU, three realisations."""
+    m = _gpu()
+    monkeypatch.setenv("MSTOPO_PATCH_TC", "1")
+    wl = workloads.small(128, 64, seed=23, kind="voids", H=H, n_eig=6, etas=(0.3, 0.5, 0.7),
+                         rmin=2.0, beta=8.0)
+    prob = make_problem(m, wl, "mixed", tol=1e-10)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
     u, infos = prob.solve(cuda(wl.force), -1)
     ref = pipeline.run(wl, "direct", with_grad=False)
     grid, K0, oprob, _ = pipeline.build(wl)
