@@ -505,11 +505,12 @@ def run_workload(args):
     f = torch.from_numpy(np.ascontiguousarray(wl.force)).cuda()
     rho = torch.from_numpy(np.ascontiguousarray(wl.rho)).cuda()
     out.update({"mesh": [wl.nelx, wl.nely], "dofs": 2 * (wl.nelx + 1) * (wl.nely + 1),
-                "realisations": len(wl.etas)})
+                "realisations": len(wl.etas), "preconditioner": args.preconditioner})
     precisions = ["mixed"] if args.workload_mixed_only else ["mixed", "fp64"]
     for prec in precisions:
         prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
-                         penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=1e-8)
+                         penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=1e-8,
+                         preconditioner=args.preconditioner, max_iter=5000)
         torch.cuda.synchronize()
         t0 = time.time()
         prob.set_design(rho, wl.rmin, wl.beta, wl.etas, wl.cell)
@@ -595,6 +596,9 @@ def main():
                     help="run the whole path on a named workload (mbb_c1, mbb_c2, mbb_c3, mbb_c5, "
                          "cantilever_batch) and print one JSON line (no benchmark)")
     ap.add_argument("--workload-mixed-only", action="store_true")
+    ap.add_argument("--preconditioner", default="additive", choices=["additive", "sgs"],
+                    help="with --workload-run: the additive two-level Schwarz preconditioner, or "
+                         "the paper's multiplicative one (SGS, coarse correction, SGS)")
     args = ap.parse_args()
     if args.only:
         run_only(args)

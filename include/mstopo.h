@@ -60,6 +60,18 @@ typedef enum {
 } mstopo_coarse_solver;
 
 typedef enum {
+  MSTOPO_PREC_ADDITIVE = 0,       /* two-level additive Schwarz: spectral coarse solve plus the
+                                     overlapping exact patch solves on every agglomerate     */
+  MSTOPO_PREC_MULTIPLICATIVE_SGS = 1  /* the paper's own preconditioner (Sec. 2.4.2): one
+                                     symmetric Gauss-Seidel sweep, the spectral coarse
+                                     correction, a second sweep, applied multiplicatively.
+                                     The sweeps visit the nodes in 4 colours, (i mod 2) +
+                                     2 (j mod 2), solving each node's 2x2 block; the operator
+                                     is symmetric positive definite, so the flexible CG runs
+                                     it unchanged. No patch factors are built. */
+} mstopo_preconditioner;
+
+typedef enum {
   MSTOPO_FIELD_RHO_TILDE = 0,  /* filtered design (design layout)                         */
   MSTOPO_FIELD_RHO_BAR = 1,    /* projected density of one realisation (design layout)    */
   MSTOPO_FIELD_YOUNG = 2       /* SIMP Young's modulus of one realisation (element layout) */
@@ -92,6 +104,7 @@ typedef struct {
                                 the iterations of the first solve after the last build, the
                                 next all-realisation solve first rebuilds the preconditioner on
                                 the design set then (0 = never rebuild automatically) */
+  int32_t preconditioner;    /* mstopo_preconditioner                                       */
 } mstopo_problem;
 
 typedef struct {

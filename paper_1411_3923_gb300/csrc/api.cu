@@ -89,7 +89,9 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             d->nu >= 0.0 && d->nu < 0.5 && d->Emin > 0.0 && d->Emin <= d->E0 && d->fixed != nullptr &&
             d->tol > 0.0 && d->max_iter > 0 && d->local_shift >= 0.0 && d->rebuild_ratio >= 0.0 &&
             (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 32 &&
-            d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI;
+            d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI &&
+            (d->preconditioner == MSTOPO_PREC_ADDITIVE ||
+             d->preconditioner == MSTOPO_PREC_MULTIPLICATIVE_SGS);
   if (!ok) {
     h->err = "invalid problem description";
     return fail(MSTOPO_INVALID_ARG);

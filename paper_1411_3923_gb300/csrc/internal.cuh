@@ -155,6 +155,8 @@ struct Precond {
   unsigned char* d_ptc = nullptr;
   long long tc_line_bytes = 0;
   int patch_tc = 0;
+  int kind = 0;                     // mstopo_preconditioner
+  void* d_sgs = nullptr;            // multiplicative SGS: [2][MSTOPO_MAX_SYS][n_dof] doubles of work space
   // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
   double* d_lambda = nullptr; double* d_psi64 = nullptr; float* d_psi32 = nullptr;
   double* d_eigres = nullptr;       // [T] residual norms
@@ -288,3 +290,7 @@ size_t patch_tc_smem(int nb, int nst);
 cudaError_t patch_tc_pack(const double* Linv, const double* W, const double* V, int T, int nb,
                           int NL, unsigned char* out, cudaStream_t s);
 cudaError_t patch_tc_solve(mstopo_handle* h, int Q, const float* r, int sys0, int nsys, float* Xg);
+// the paper's multiplicative SGS two-level preconditioner (csrc/smoother.cu); part 0 = the
+// operator, 2 = one symmetric sweep from zero
+cudaError_t sgs_apply_f64(mstopo_handle* h, const double* r, double* z, int sys0, int nsys, int part);
+cudaError_t sgs_apply_f32(mstopo_handle* h, const float* r, float* z, int sys0, int nsys, int part);

@@ -1159,7 +1159,7 @@ void precond_free(Precond& pc) {
   dfree(pc.d_Kc); dfree(pc.d_Kcinv);
   dfree(pc.d_cLinv); dfree(pc.d_cLinvT); dfree(pc.d_cW); dfree(pc.d_cV);
   dfree(pc.d_cy); dfree(pc.d_cx); dfree(pc.d_s2o); dfree(pc.d_cbar); dfree(pc.d_rc); dfree(pc.d_uc);
-  dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag);
+  dfree(pc.d_zp32); dfree(pc.d_zp64); dfree(pc.d_work); dfree(pc.d_flag); dfree(pc.d_sgs);
   pc = Precond();
 }
 
@@ -1179,6 +1179,9 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   // dilated design embeds the others), K_c and the patch matrices from each realisation's
   // own moduli
   const int nsv = pc.nsv = h->n_eta;
+  pc.kind = h->p.preconditioner;
+  if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS)
+    CKB(cudaMalloc(&pc.d_sgs, (size_t)2 * MSTOPO_MAX_SYS * h->n_dof * sizeof(double)));
   const double* E = h->d_E64 + (long long)ref * h->n_el;
   K0P K0;
   for (int q = 0; q < 64; ++q) K0.k[q] = h->K0[q];
@@ -1688,11 +1691,15 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
 cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int sys0, int nsys,
                               int part) {
   Precond& pc = h->pc;
+  if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS && part != 1)
+    return sgs_apply_f64(h, r, z, sys0, nsys, part);
   return apply_impl<double>(h, r, z, sys0, nsys, part, pc.d_psi64, pc.d_pf64, pc.d_pb64, pc.d_zp64);
 }
 
 cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sys0, int nsys,
                               int part) {
   Precond& pc = h->pc;
+  if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS && part != 1)
+    return sgs_apply_f32(h, r, z, sys0, nsys, part);
   return apply_impl<float>(h, r, z, sys0, nsys, part, pc.d_psi32, pc.d_pf32, pc.d_pb32, pc.d_zp32);
 }

@@ -35,7 +35,7 @@ class _Problem(C.Structure):
                 ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("local_shift", C.c_double), ("stream", C.c_void_p),
                 ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32),
-                ("rebuild_ratio", C.c_double)]
+                ("rebuild_ratio", C.c_double), ("preconditioner", C.c_int32)]
 
 
 class _BuildInfo(C.Structure):
@@ -53,6 +53,7 @@ class _Stats(C.Structure):
 
 
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
+PRECONDITIONERS = {"additive": 0, "sgs": 1}   # mstopo_preconditioner
 
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
 
@@ -139,7 +140,8 @@ class Problem:
                  n_eig: int = 4, lambda_thresh: float = 0.0, precision: str = "mixed",
                  tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
                  stream: Optional[int] = None, coarse_solver: str = "auto",
-                 reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0):
+                 reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0,
+                 preconditioner: str = "additive"):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
@@ -147,7 +149,8 @@ class Problem:
         d = _Problem(nelx, nely, nu, E0, Emin, penal, self._fixed.ctypes.data, H, n_eig,
                      lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
                      local_shift, stream, COARSE_SOLVERS[coarse_solver],
-                     1 if reuse_preconditioner else 0, rebuild_ratio)
+                     1 if reuse_preconditioner else 0, rebuild_ratio,
+                     PRECONDITIONERS[preconditioner])
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:

@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import workloads
-from oracle import design, fem, msfem, pipeline
+from oracle import design, fem, msfem, pipeline, smoother
 
 
 def _gpu():
@@ -493,3 +493,88 @@ def test_basis_update_rule(ratio, rebuilds):
     for inf in i1 + i2 + i3:
         assert inf["status"] == 0
         assert inf["compliance"] == pytest.approx(ref["c"][0], rel=1e-9)
+
+
+# ---------------------------------------------------------------- the paper's preconditioner
+def _free_vec(grid, oprob, v):
+    return grid.nodal_from_neutral(np.asarray(v))[oprob.free]
+
+
+def _neutral(grid, oprob, vf):
+    z = np.zeros(grid.n_dof)
+    z[oprob.free] = vf
+    return grid.nodal_to_neutral(z)
+
+
+@pytest.mark.parametrize("size,bc", [((28, 12), "mbb"), ((33 * 4, 5 * 4), "cantilever")])
+def test_sgs_sweep_matches_oracle(size, bc):
+    """One symmetric node-block Gauss-Seidel sweep from zero (colours 0..3, then 3..0;
+    apply_precond part 2 of the multiplicative preconditioner) against the oracle's
+    colour sweep: FP64 to round-off, FP32 to its unit round-off times the conditioning
+    of the 2x2 node blocks."""
+    m = _gpu()
+    wl = workloads.small(*size, seed=31, kind="voids", bc=bc, H=4, n_eig=4, Emin=1e-3)
+    prob = make_problem(m, wl, "mixed", preconditioner="sgs")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    grid, K0, oprob, chain = pipeline.build(wl)
+    E = chain.forward(wl.rho)["E"][0]
+    K = oprob.free_matrix(E)
+    S = smoother.SymmetricGaussSeidel(oprob, K, "colour")
+    r = np.random.default_rng(9).standard_normal((wl.nely + 1, wl.nelx + 1, 2))
+    rf = _free_vec(grid, oprob, r)
+    z_ref = _neutral(grid, oprob, S.sweep(np.zeros_like(rf), rf))
+    z = prob.apply_precond(cuda(r), m.FP64, 2).cpu().numpy()
+    assert np.linalg.norm(z - z_ref) <= 1e-12 * np.linalg.norm(z_ref)
+    z32 = prob.apply_precond(cuda(r), m.MIXED, 2).cpu().numpy()
+    assert np.linalg.norm(z32 - z_ref) <= 1e-4 * np.linalg.norm(z_ref)
+
+
+def test_multiplicative_sgs_operator_matches_oracle():
+    """SGS, coarse correction, SGS (Sec. 2.4.2) against the oracle's operator (the coarse
+    space within the eigen-solve's tolerance) and symmetric to round-off."""
+    m = _gpu()
+    wl = workloads.small(64, 32, seed=32, kind="voids", H=8, n_eig=4, Emin=1e-3)
+    prob = make_problem(m, wl, "fp64", preconditioner="sgs")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    grid, K0, oprob, chain = pipeline.build(wl)
+    E = chain.forward(wl.rho)["E"][0]
+    K = oprob.free_matrix(E)
+    tl = msfem.TwoLevel(oprob, E, wl.H, wl.n_eig, with_patches=False)
+    Mref = smoother.MultiplicativeTwoLevel(K, smoother.SymmetricGaussSeidel(oprob, K, "colour"),
+                                           tl.coarse)
+    rng = np.random.default_rng(10)
+    a = rng.standard_normal((wl.nely + 1, wl.nelx + 1, 2))
+    b = rng.standard_normal((wl.nely + 1, wl.nelx + 1, 2))
+    fa, fb = _free_vec(grid, oprob, a), _free_vec(grid, oprob, b)
+    za = prob.apply_precond(cuda(a), m.FP64, 0).cpu().numpy()
+    zb = prob.apply_precond(cuda(b), m.FP64, 0).cpu().numpy()
+    z_ref = _neutral(grid, oprob, Mref.apply(fa))
+    assert np.linalg.norm(za - z_ref) <= 1e-6 * np.linalg.norm(z_ref)
+    ga, gb = _free_vec(grid, oprob, za), _free_vec(grid, oprob, zb)
+    assert abs(ga @ fb - fa @ gb) <= 1e-10 * np.linalg.norm(ga) * np.linalg.norm(fb)
+    assert ga @ fa > 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("etas", [(0.5,), (0.3, 0.5, 0.7)])
+def test_solve_with_multiplicative_sgs(precision, etas):
+    """The flexible CG with the paper's multiplicative SGS preconditioner converges to the
+    sparse-LU solution of every realisation."""
+    m = _gpu()
+    wl = workloads.small(96, 48, seed=33, kind="voids", H=8, n_eig=6, etas=etas, rmin=2.0,
+                         beta=8.0)
+    prob = make_problem(m, wl, precision, tol=1e-10, preconditioner="sgs")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    u, infos = prob.solve(cuda(wl.force), -1)
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    grid, K0, oprob, _ = pipeline.build(wl)
+    for k, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        Kf = oprob.free_matrix(ref["E"][k])
+        ug = grid.nodal_from_neutral(u[k].cpu().numpy())[oprob.free]
+        ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
+        assert msfem.energy_error(Kf, ur, ug) < 1e-6
+        assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-9)
