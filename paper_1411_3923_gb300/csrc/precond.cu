@@ -1180,7 +1180,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   // own moduli
   const int nsv = pc.nsv = h->n_eta;
   pc.kind = h->p.preconditioner;
-  if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS)
+  const bool sgs = pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS;   // no patch solves to build
+  if (sgs)
     CKB(cudaMalloc(&pc.d_sgs, (size_t)2 * MSTOPO_MAX_SYS * h->n_dof * sizeof(double)));
   const double* E = h->d_E64 + (long long)ref * h->n_el;
   K0P K0;
@@ -1230,7 +1231,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   const int NA = pc.NA, nbA = pc.nbA, NP = pc.NP, nbP = pc.nbP;
   const long long nnA = (long long)nbA * nbA, nA = (long long)NA * nbA;
   const long long nnP = nnA, nP = nA;
-  const int TP = T * nsv;             // patch operators
+  const int TP = sgs ? 0 : T * nsv;   // patch operators
   const int NS = T + TP;              // factorised systems
   // subspace dimension: 2k + 4 rounded up to a multiple of the cluster size (compile-time variants)
   const int q = std::min(((2 * pc.kmax + 4) + EIG_CL - 1) / EIG_CL * EIG_CL, 2 * MSTOPO_MAX_EIG);
@@ -1243,12 +1244,12 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaMalloc(&dC, (size_t)NS * (NA - 1) * nnA * 8));
   CKB(cudaMalloc(&dS, (size_t)NS * nnA * 8));
   CKB(cudaMalloc(&dfree_, (size_t)T * nA));
-  CKB(cudaMalloc(&pc.d_pfree, (size_t)TP * nP));
+  if (TP) CKB(cudaMalloc(&pc.d_pfree, (size_t)TP * nP));
   CKB(cudaMalloc(&d_st, (size_t)std::max(NS, 2) * sizeof(int)));
   note_launch(), k_assemble_box<<<dim3(T, NA), PC_THREADS, 0, s>>>(E, h->d_nmask, h->nelx, h->nely, d_rep, H,
                                                     pc.ncx, 0, K0, dA, dB, dfree_);
   CKB(cudaGetLastError());
-  for (int k = 0; k < nsv; ++k) {
+  for (int k = 0; k < nsv && !sgs; ++k) {
     const size_t o = (size_t)T + (size_t)k * T;
     note_launch(), k_assemble_box<<<dim3(T, NP), PC_THREADS, 0, s>>>(h->d_E64 + (long long)k * h->n_el, h->d_nmask,
                                                       h->nelx, h->nely, d_rep, H, pc.ncx, 1, K0,
@@ -1260,7 +1261,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   uint8_t* dfree2;
   CKB(cudaMalloc(&dfree2, (size_t)NS * nA));
   CKB(cudaMemcpyAsync(dfree2, dfree_, (size_t)T * nA, cudaMemcpyDeviceToDevice, s));
-  CKB(cudaMemcpyAsync(dfree2 + (size_t)T * nA, pc.d_pfree, (size_t)TP * nP, cudaMemcpyDeviceToDevice, s));
+  if (TP) CKB(cudaMemcpyAsync(dfree2 + (size_t)T * nA, pc.d_pfree, (size_t)TP * nP, cudaMemcpyDeviceToDevice, s));
   note_launch(), k_bt_factor<<<NS, PC_THREADS, 0, s>>>(dA, dB, dfree2, EIG_SHIFT, pc.local_shift, T, nbA, NA,
                                                        dLi, dC, dS, d_st);
   CKB(cudaGetLastError());
@@ -1345,7 +1346,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   // lanes (stride = 16 mod 32)
   pc.nbs = (nbP + 3) / 4 * 4;
   while (pc.nbs % 32 != (patch_s(Qp) == 16 ? 16 : 8)) pc.nbs += 4;
-  {
+  if (!sgs) {
     const double* pLi = dLi + (size_t)T * NA * nnA;
     const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
     double *dW, *dV;
@@ -1549,13 +1550,15 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     return e;
   };
   CKB(cudaStreamSynchronize(s));
-  CKB(build_groups(pc.pg[0], P));
-  if (pc.patch_tc) CKB(build_groups(pc.pg[1], PATCH_COLS));
+  if (!sgs) CKB(build_groups(pc.pg[0], P));
+  if (!sgs && pc.patch_tc) CKB(build_groups(pc.pg[1], PATCH_COLS));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   const size_t xg = (size_t)std::max(pc.pg[0].n, pc.pg[1].n) * nP * PATCH_COLS;
-  CKB(cudaMalloc(&pc.d_zp32, xg * 4));
-  CKB(cudaMalloc(&pc.d_zp64, xg * 8));
+  if (xg) {
+    CKB(cudaMalloc(&pc.d_zp32, xg * 4));
+    CKB(cudaMalloc(&pc.d_zp64, xg * 8));
+  }
   CKB(cudaEventRecord(ev[5], s));
   // build report
   std::vector<double> eres(T);
