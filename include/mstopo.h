@@ -225,9 +225,14 @@ mstopo_status mstopo_apply_K_f32(mstopo_handle* h, int32_t realisation, const fl
 #define MSTOPO_INPUT_MASKED 1
 mstopo_status mstopo_apply_K_f32_ex(mstopo_handle* h, int32_t realisation, const float* u, float* y,
                                     int32_t flags);
-/* z = M^-1 r with the built two-level preconditioner (coarse + overlapping patch solves),
- * in the given precision.  part: 0 = both levels, 1 = coarse only R_c^T K_c^-1 R_c r,
- * 2 = patches only.  r, z: DEVICE nodal layout. */
+/* z = M^-1 r with the built two-level preconditioner, in the given precision.
+ * Additive (MSTOPO_PREC_ADDITIVE): part 0 = both levels, 1 = coarse only
+ * R_c^T K_c^-1 R_c r, 2 = patches only.
+ * Multiplicative (MSTOPO_PREC_MULTIPLICATIVE_SGS, Sec. 2.4.2): part 0 = the operator (SGS,
+ * coarse correction of the residual, SGS), 1 = coarse only, 2 = one symmetric Gauss-Seidel
+ * sweep from zero (the smoother alone).
+ * r, z: DEVICE nodal layout, one realisation (realisation 0).  Errors: INVALID_ARG, NOT_READY
+ * (no preconditioner built), CUDA_ERROR. */
 mstopo_status mstopo_apply_precond(mstopo_handle* h, int32_t precision, int32_t part,
                                    const double* r, double* z);
 /* Eigenpairs kept for the agglomerate of coarse node (I, J) (Sec. 2.4):

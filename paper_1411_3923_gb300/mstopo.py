@@ -133,7 +133,13 @@ def _dev(t: torch.Tensor, dtype=torch.float64) -> torch.Tensor:
 
 
 class Problem:
-    """One mesh with its boundary conditions: design chain, preconditioner and solves."""
+    """One mesh with its boundary conditions: design chain, preconditioner and solves.
+
+    ``preconditioner``: "additive" (two-level additive Schwarz: spectral coarse solve plus the
+    overlapping exact patch solves) or "sgs" (the paper's own, Sec. 2.4.2: a symmetric
+    Gauss-Seidel sweep, the coarse correction, a second sweep, applied multiplicatively).
+    ``coarse_solver``: "auto", "dense" or "blocktri" for K_c u_c = r_c.
+    ``precision``: "mixed" (FP64 outer solve, FP32 inner arithmetic) or "fp64"."""
 
     def __init__(self, nelx: int, nely: int, fixed: np.ndarray, *, nu: float = 0.3,
                  E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
