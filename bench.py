@@ -156,6 +156,17 @@ def cpu_baseline(full_dofs: int, scale: int = 8) -> dict:
 
 
 # ------------------------------------------------------------------------------ our arm
+def max_over_ranks(values, world: int, device="cpu"):
+    """Each timing's maximum over the ranks: the replicas run concurrently, so the slowest
+    one sets the job's time.  One all-reduce over the default process group (NCCL on the
+    GPUs; any backend works)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_ours(args, rank: int, world: int):
     import numpy as np
     import torch
@@ -361,10 +372,8 @@ def run_ours(args, rank: int, world: int):
            "api": "mstopo_solve_host (pinned host f in, u out)"}
 
     # ---- max over ranks ----
-    vals = torch.tensor([solve_ms, step_ms, fp64_ms, e2e["value"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    solve_ms, step_ms, fp64_ms, e2e_v = vals.tolist()
+    solve_ms, step_ms, fp64_ms, e2e_v = max_over_ranks([solve_ms, step_ms, fp64_ms, e2e["value"]],
+                                                       world, dev)
     e2e["value"] = e2e_v
     if rank != 0:
         return None
