@@ -44,3 +44,33 @@ def test_invalid_problem_is_rejected_without_gpu_work():
     assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1      # 8 % 3 != 0
     assert h.value is None
     assert b"invalid" in lib.mstopo_last_error(None)
+
+
+@pytest.mark.parametrize("c_name,py_name", [("mstopo_problem", "_Problem"),
+                                             ("mstopo_build_info", "_BuildInfo"),
+                                             ("mstopo_solve_info", "_SolveInfo"),
+                                             ("mstopo_stats", "_Stats")])
+def test_ctypes_structs_match_the_header_layout(tmp_path, c_name, py_name):
+    """Every public struct of include/mstopo.h has the same size and field offsets in the
+    binding's ctypes mirror: a C program compiled against the header prints them."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1411_3923_gb300 import mstopo
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    py = getattr(mstopo, py_name)
+    fields = [f[0] for f in py._fields_]
+    lines = [f'printf("size %zu\\n", sizeof({c_name}));']
+    lines += [f'printf("{f} %zu\\n", offsetof({c_name}, {f}));' for f in fields]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"mstopo.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(py), (c_name, out["size"], ctypes.sizeof(py))
+    for f in fields:
+        assert int(out[f]) == getattr(py, f).offset, (c_name, f)
