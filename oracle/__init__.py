@@ -17,7 +17,8 @@ msfem     agglomerates, local generalised eigenproblems with diagonal weighting,
           two-level preconditioner and PCG (Sec. 2.4, 3.2)
 smoother  the paper's own preconditioner: symmetric Gauss-Seidel before and after the
           spectral coarse solve, applied multiplicatively (Sec. 2.4.2), with the
-          lexicographic point sweep and the GPU's colour-by-colour node-block sweep
+          lexicographic point sweep and the GPU's colour-by-colour node-block sweep, and
+          the paper's outer method, right-preconditioned restarted GMRES
 pipeline  the whole hot path on one workload (Sec. 5.3 for the shared preconditioner)
 
 Pins: every function here is checked by tests/test_oracle_*.py against closed forms,

@@ -23,6 +23,10 @@ one after):
 With a symmetric smoother before and after, the operator is symmetric positive definite
 (error propagation (I - S K)(I - C K)(I - S K), S the symmetric sweep), so PCG applies to it,
 as the paper remarks for its preconditioner.
+
+The paper's outer method is GMRES (Sec. 2.4.2): ``gmres`` is right-preconditioned restarted
+GMRES(m) written from its textbook definition (Arnoldi with modified Gram-Schmidt, Givens
+rotations), stopped on the true residual.
 """
 from __future__ import annotations
 
@@ -109,3 +113,57 @@ class MultiplicativeTwoLevel:
         x = self.S.sweep(np.zeros_like(r), r)
         x = x + self.coarse(r - self.K @ x)
         return self.S.sweep(x, r)
+
+
+def gmres(K: sp.spmatrix, f: np.ndarray, Minv, tol: float = 1e-8, restart: int = 50,
+          maxit: int = 1000, x0=None, history: list | None = None):
+    """Right-preconditioned restarted GMRES(m), the paper's outer method (Sec. 2.4.2):
+    Arnoldi on K M^-1 with modified Gram-Schmidt, Givens rotations for the small least-squares
+    problem, x = x0 + M^-1 V y.  Stops when the TRUE relative residual ||f - K x|| / ||f|| is
+    at most tol (checked at every restart and whenever the recurrence estimate reaches tol).
+    ``history`` (optional) receives the recurrence residual norm after every iteration.
+    Returns (x, iterations, true relative residual)."""
+    x = np.zeros_like(f) if x0 is None else x0.copy()
+    nf = np.linalg.norm(f)
+    if nf == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while it < maxit:
+        r = f - K @ x
+        beta = np.linalg.norm(r)
+        if beta <= tol * nf:
+            break
+        m = min(restart, maxit - it)
+        V = np.zeros((m + 1, f.size))
+        Z = np.zeros((m, f.size))
+        Hm = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            Z[j] = Minv(V[j])
+            w = K @ Z[j]
+            for i in range(j + 1):                     # modified Gram-Schmidt
+                Hm[i, j] = w @ V[i]
+                w = w - Hm[i, j] * V[i]
+            Hm[j + 1, j] = np.linalg.norm(w)
+            if Hm[j + 1, j] > 0.0:
+                V[j + 1] = w / Hm[j + 1, j]
+            for i in range(j):                         # earlier rotations on the new column
+                a, b = Hm[i, j], Hm[i + 1, j]
+                Hm[i, j], Hm[i + 1, j] = cs[i] * a + sn[i] * b, -sn[i] * a + cs[i] * b
+            d = np.hypot(Hm[j, j], Hm[j + 1, j])        # new rotation zeroes H[j+1, j]
+            cs[j], sn[j] = Hm[j, j] / d, Hm[j + 1, j] / d
+            Hm[j, j], Hm[j + 1, j] = d, 0.0
+            g[j], g[j + 1] = cs[j] * g[j], -sn[j] * g[j]
+            it += 1
+            j_done = j + 1
+            if history is not None:
+                history.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= tol * nf or Hm[j, j] == 0.0:
+                break
+        y = np.linalg.solve(np.triu(Hm[:j_done, :j_done]), g[:j_done])
+        x = x + Z[:j_done].T @ y
+    return x, it, np.linalg.norm(f - K @ x) / nf

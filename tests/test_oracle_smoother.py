@@ -122,3 +122,48 @@ def test_pcg_with_multiplicative_preconditioner_matches_direct_solve():
     assert rr <= 1e-10 and msfem.energy_error(K, u, x) < 1e-6
     _, it_one, _ = msfem.pcg(K, f, lambda v: S.sweep(np.zeros_like(v), v), tol=1e-10, maxit=4000)
     assert 2 * it < it_one
+
+
+def test_gmres_converges_in_as_many_steps_as_distinct_eigenvalues():
+    """Unpreconditioned GMRES on a diagonal matrix with 4 distinct eigenvalues: the Krylov
+    space holds the solution after exactly 4 steps, not before."""
+    vals = np.tile([1.0, 2.0, 3.0, 5.0], 10)
+    K = sp.diags(vals).tocsr()
+    f = np.random.default_rng(11).standard_normal(vals.size)
+    hist = []
+    x, it, rr = smoother.gmres(K, f, lambda v: v, tol=1e-12, restart=20, history=hist)
+    assert it == 4 and rr <= 1e-12
+    assert hist[2] > 1e-6 * np.linalg.norm(f)
+    assert np.allclose(x, f / vals, rtol=1e-12, atol=1e-12)
+
+
+def test_gmres_residual_never_exceeds_pcg_residual():
+    """Right-preconditioned GMRES and PCG (x0 = 0, the same SPD preconditioner) search the
+    same affine Krylov space; GMRES minimises the 2-norm of the residual over it, so at every
+    step its residual is at most PCG's."""
+    wl, grid, prob, E, K = setup(16, 8, H=4, seed=12, Emin=1e-3)
+    tl = msfem.TwoLevel(prob, E, wl.H, wl.n_eig, with_patches=False)
+    M = smoother.MultiplicativeTwoLevel(K, smoother.SymmetricGaussSeidel(prob, K, "colour"),
+                                        tl.coarse)
+    f = grid.nodal_from_neutral(wl.force)[prob.free]
+    hist = []
+    smoother.gmres(K, f, M.apply, tol=1e-13, restart=100, maxit=12, history=hist)
+    for j in range(1, min(12, len(hist)) + 1):
+        xp, itp, _ = msfem.pcg(K, f, M.apply, tol=1e-300, maxit=j)
+        assert itp == j
+        assert hist[j - 1] <= np.linalg.norm(f - K @ xp) * (1 + 1e-8) + 1e-14 * np.linalg.norm(f)
+
+
+def test_gmres_with_multiplicative_preconditioner_matches_direct_solve():
+    """The paper's solver (GMRES + coarse/SGS multiplicative preconditioner) against sparse
+    LU, at contrast 1e9."""
+    wl, grid, prob, E, K = setup(32, 16, H=8, seed=13, Emin=1e-9, n_eig=4)
+    tl = msfem.TwoLevel(prob, E, wl.H, wl.n_eig, with_patches=False)
+    M = smoother.MultiplicativeTwoLevel(K, smoother.SymmetricGaussSeidel(prob, K, "colour"),
+                                        tl.coarse)
+    f = grid.nodal_from_neutral(wl.force)[prob.free]
+    u = spla.splu(K.tocsc()).solve(f)
+    x, it, rr = smoother.gmres(K, f, M.apply, tol=1e-10, restart=200, maxit=2000)
+    assert rr <= 1e-10 and msfem.energy_error(K, u, x) < 1e-6
+    _, it_pcg, _ = msfem.pcg(K, f, M.apply, tol=1e-10, maxit=2000)
+    assert it <= it_pcg + 2
