@@ -19,6 +19,8 @@ smoother  the paper's own preconditioner: symmetric Gauss-Seidel before and afte
           spectral coarse solve, applied multiplicatively (Sec. 2.4.2), with the
           lexicographic point sweep and the GPU's colour-by-colour node-block sweep, and
           the paper's outer method, right-preconditioned restarted GMRES
+pde_filter  the PDE (Helmholtz) density filter with periodicity and connectivity imposed by
+          collapsed DOFs, for designs of several microstructure blocks (Sec. 4.3, 4.5)
 pipeline  the whole hot path on one workload (Sec. 5.3 for the shared preconditioner)
 
 Pins: every function here is checked by tests/test_oracle_*.py against closed forms,
