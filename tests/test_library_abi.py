@@ -74,3 +74,18 @@ def test_ctypes_structs_match_the_header_layout(tmp_path, c_name, py_name):
     assert int(out["size"]) == ctypes.sizeof(py), (c_name, out["size"], ctypes.sizeof(py))
     for f in fields:
         assert int(out[f]) == getattr(py, f).offset, (c_name, f)
+
+
+def test_unknown_preconditioner_kind_is_rejected():
+    import ctypes
+    import numpy as np
+    import paper_1411_3923_gb300 as m
+    from paper_1411_3923_gb300 import mstopo
+    lib = m.load()
+    fixed = np.zeros(2 * 9 * 5, np.uint8)
+    for kind, ok in ((7, False), (-1, False)):
+        d = mstopo._Problem(8, 4, 0.3, 1.0, 1e-9, 3.0, fixed.ctypes.data, 4, 4, 0.0, 1, 1e-8, 100,
+                            0.0, None, 0, 0, 0.0, kind)
+        h = ctypes.c_void_p()
+        assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1
+        assert h.value is None
