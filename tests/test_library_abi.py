@@ -82,9 +82,10 @@ def test_unknown_preconditioner_kind_is_rejected():
     import paper_1411_3923_gb300 as m
     from paper_1411_3923_gb300 import mstopo
     lib = m.load()
-    fixed = np.zeros(2 * 9 * 5, np.uint8)
-    for kind, ok in ((7, False), (-1, False)):
-        d = mstopo._Problem(8, 4, 0.3, 1.0, 1e-9, 3.0, fixed.ctypes.data, 4, 4, 0.0, 1, 1e-8, 100,
+    fixed = np.zeros(2 * 9 * 9, np.uint8)
+    # valid in every other field (8x8 elements, H 4: two coarse cells each way)
+    for kind in (7, -1):
+        d = mstopo._Problem(8, 8, 0.3, 1.0, 1e-9, 3.0, fixed.ctypes.data, 4, 4, 0.0, 1, 1e-8, 100,
                             0.0, None, 0, 0, 0.0, kind)
         h = ctypes.c_void_p()
         assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1
