@@ -21,6 +21,8 @@ smoother  the paper's own preconditioner: symmetric Gauss-Seidel before and afte
           the paper's outer method, right-preconditioned restarted GMRES
 pde_filter  the PDE (Helmholtz) density filter with periodicity and connectivity imposed by
           collapsed DOFs, for designs of several microstructure blocks (Sec. 4.3, 4.5)
+optimise  the design loop: MMA (one constraint, dual by bisection) on the robust compliance
+          with the expected-volume constraint, and the continuation schedule (Sec. 4.4, 4.5)
 pipeline  the whole hot path on one workload (Sec. 5.3 for the shared preconditioner)
 
 Pins: every function here is checked by tests/test_oracle_*.py against closed forms,
