@@ -148,3 +148,15 @@ def optimise(wl, volfrac: float, stages, kappa: float = 1.0, rel_change: float =
             f_prev = f
             rho = mma.step(rho.ravel(), f, df.ravel(), g, dg.ravel()).reshape(rho.shape)
     return rho
+
+
+def robust_verification(wl, rho: np.ndarray, etas) -> np.ndarray:
+    """Compliance of one design over many thresholds (Sec. 4.4 verifies final designs on
+    uniformly distributed eta in [0.3, 0.7]); direct state solves, one realisation each."""
+    import copy
+    out = []
+    for eta in etas:
+        w = copy.copy(wl)
+        w.rho, w.etas = np.asarray(rho, float), (float(eta),)
+        out.append(pipeline.run(w, "direct", with_grad=False)["c"][0])
+    return np.array(out)

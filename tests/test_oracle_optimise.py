@@ -77,3 +77,12 @@ def test_design_loop_lowers_the_robust_compliance_within_the_volume():
     assert f1[-1] < f1[0] / 3.0
     assert f2[-1] < 0.97 * f2[0]
     assert -0.05 <= hist[-1]["g"] <= 1e-3
+
+
+def test_robust_verification_compliance_rises_with_the_threshold():
+    """A higher threshold eta erodes the projected design pointwise, so the stiffness falls
+    in the Loewner order and the compliance f^T K^-1 f rises: monotone over eta in [0.3, 0.7]."""
+    wl = workloads.small(24, 8, seed=6, kind="random", rmin=1.5, beta=4.0, Emin=1e-6)
+    etas = np.linspace(0.3, 0.7, 21)
+    c = optimise.robust_verification(wl, wl.rho, etas)
+    assert np.all(np.diff(c) > 0.0)
