@@ -72,6 +72,17 @@ typedef enum {
 } mstopo_preconditioner;
 
 typedef enum {
+  MSTOPO_PATCH_AUTO = 0,           /* by problem size: the tensor cores from 32 patch solves per SM */
+  MSTOPO_PATCH_CUDA_CORES = 1,     /* FP32 and FP64 patch solves on the CUDA cores              */
+  MSTOPO_PATCH_TENSOR_CORES = 2    /* MIXED: FP32 patch solves on the tensor cores (TF32 pairs) */
+} mstopo_patch_kernel;
+
+/* mstopo_problem.exec_flags (bits; 0 = defaults) */
+#define MSTOPO_EXEC_NO_GRAPHS 1       /* run every flexible-CG iteration as direct launches      */
+#define MSTOPO_EXEC_NO_SIDE_STREAM 2  /* run the preconditioner's coarse chain on the main stream
+                                         instead of a side stream beside the patch solves        */
+
+typedef enum {
   MSTOPO_FIELD_RHO_TILDE = 0,  /* filtered design (design layout)                         */
   MSTOPO_FIELD_RHO_BAR = 1,    /* projected density of one realisation (design layout)    */
   MSTOPO_FIELD_YOUNG = 2       /* SIMP Young's modulus of one realisation (element layout) */
@@ -105,6 +116,8 @@ typedef struct {
                                 next all-realisation solve first rebuilds the preconditioner on
                                 the design set then (0 = never rebuild automatically) */
   int32_t preconditioner;    /* mstopo_preconditioner                                       */
+  int32_t patch_kernel;      /* mstopo_patch_kernel: FP32 patch solves of the additive level */
+  int32_t exec_flags;        /* MSTOPO_EXEC_* bits                                           */
 } mstopo_problem;
 
 typedef struct {
@@ -130,7 +143,8 @@ typedef struct {
 
 /* Create a handle for one mesh and boundary-condition set; allocates its device workspace.
  * Errors: INVALID_ARG (sizes not multiples of H, H outside 2..32, nelx/H < 2 or nely/H < 2, n_eig
- * outside 1..16, nu outside [0, 0.5), Emin <= 0 or Emin > E0, fixed == NULL),
+ * outside 1..16, nu outside [0, 0.5), Emin <= 0 or Emin > E0, fixed == NULL, an unknown
+ * preconditioner, coarse solver or patch kernel, unknown exec_flags bits),
  * OUT_OF_MEMORY, CUDA_ERROR.  *out is NULL on failure. */
 mstopo_status mstopo_create(const mstopo_problem* desc, mstopo_handle** out);
 void mstopo_destroy(mstopo_handle* h);

@@ -91,7 +91,9 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             (d->precision == MSTOPO_FP64 || d->precision == MSTOPO_MIXED) && d->H <= 32 &&
             d->coarse_solver >= MSTOPO_COARSE_AUTO && d->coarse_solver <= MSTOPO_COARSE_BLOCKTRI &&
             (d->preconditioner == MSTOPO_PREC_ADDITIVE ||
-             d->preconditioner == MSTOPO_PREC_MULTIPLICATIVE_SGS);
+             d->preconditioner == MSTOPO_PREC_MULTIPLICATIVE_SGS) &&
+            d->patch_kernel >= MSTOPO_PATCH_AUTO && d->patch_kernel <= MSTOPO_PATCH_TENSOR_CORES &&
+            (d->exec_flags & ~(MSTOPO_EXEC_NO_GRAPHS | MSTOPO_EXEC_NO_SIDE_STREAM)) == 0;
   if (!ok) {
     h->err = "invalid problem description";
     return fail(MSTOPO_INVALID_ARG);
@@ -113,15 +115,19 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     h->err = "could not create the side stream";
     return fail(MSTOPO_CUDA_ERROR);
   }
-  if (getenv("MSTOPO_NO_GRAPHS")) h->graphs_enabled = 0;
-  if (const char* v = getenv("MSTOPO_PATCH_TC")) h->patch_tc = atoi(v) != 0 ? 1 : 0;
-  if (getenv("MSTOPO_NO_FORK")) {   // run the preconditioner's coarse chain on the main stream
+  if (d->exec_flags & MSTOPO_EXEC_NO_GRAPHS) h->graphs_enabled = 0;
+  h->patch_tc = d->patch_kernel == MSTOPO_PATCH_AUTO ? -1 : (d->patch_kernel == MSTOPO_PATCH_TENSOR_CORES ? 1 : 0);
+  if (d->exec_flags & MSTOPO_EXEC_NO_SIDE_STREAM) {
     cudaStreamDestroy(h->s_side);
     h->s_side = nullptr;
   }
   h->nelx = d->nelx;
   h->nely = d->nely;
-  h->n_nodes = (long long)(d->nelx + 1) * (d->nely + 1);
+  h->n_nodes = ((long long)d->nelx + 1) * ((long long)d->nely + 1);
+  if (h->n_nodes > (1LL << 30)) {   // index arithmetic of the kernels stays in range
+    h->err = "mesh too large (more than 2^30 nodes)";
+    return fail(MSTOPO_INVALID_ARG);
+  }
   h->n_dof = 2 * h->n_nodes;
   h->n_el = (long long)d->nelx * d->nely;
   element_stiffness_closed_form(d->nu, h->K0);

@@ -10,10 +10,10 @@
 
 #define NOALLOC_MAX_DOFS (1LL << 22)          // 4,194,304 DOFs = 2,097,152 nodes
 #define NOALLOC_MAX_DEVICES 64
-static const size_t kNoallocBytes = (size_t)NOALLOC_MAX_DOFS * 4 * 2 + (size_t)NOALLOC_MAX_DOFS / 2;
-
 // [u32: MAX_DOFS floats][y32: MAX_DOFS floats][node mask: MAX_DOFS/2 bytes]
-static __device__ __align__(256) unsigned char g_noalloc_scratch[(1LL << 22) * 4 * 2 + (1LL << 21)];
+#define NOALLOC_BYTES (NOALLOC_MAX_DOFS * 4 * 2 + NOALLOC_MAX_DOFS / 2)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 static std::mutex g_noalloc_mu;
@@ -47,10 +47,10 @@ extern "C" mstopo_status mstopo_apply_K_f32_noalloc(const double* u, double* y, 
                                                    int32_t nely, double nu, void* stream) {
   if (!u || !y || !E || !fixed || nelx <= 0 || nely <= 0 || !(nu >= 0.0 && nu < 0.5))
     return MSTOPO_INVALID_ARG;
-  const long long n_nodes = (long long)(nelx + 1) * (nely + 1);
+  // sizes in 64 bits before any addition (nelx = INT32_MAX must not wrap to a small count)
+  const long long n_nodes = ((long long)nelx + 1) * ((long long)nely + 1);
   const long long n_dof = 2 * n_nodes;
-  if (n_dof > NOALLOC_MAX_DOFS) return MSTOPO_INVALID_ARG;
-  (void)kNoallocBytes;
+  if (n_dof <= 0 || n_dof > NOALLOC_MAX_DOFS) return MSTOPO_INVALID_ARG;
   void* base = nullptr;
   if (noalloc_scratch(&base) != cudaSuccess) return MSTOPO_CUDA_ERROR;
   float* u32 = reinterpret_cast<float*>(base);

@@ -127,6 +127,14 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return false;
 }
 
+// wait for work this CTA issued itself (bulk copies, MMAs) before it frees TMEM and exits: an
+// abort of another role does not cut it short, only the iteration limit does
+__device__ __forceinline__ void tc_drain(uint64_t* bar, uint32_t parity, int* err) {
+  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return;
+  atomicExch(err, (int)MSTOPO_TIMEOUT);
+}
+
 // the same wait for a whole warp: lane 0 polls, the warp takes its result (and its ordering)
 __device__ __forceinline__ bool tc_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort,
                                              int* err) {
@@ -146,19 +154,6 @@ __device__ __forceinline__ int b_off(int n, int c, int sbo) {
 
 }  // namespace
 
-#ifdef MSTOPO_TC_TRACE
-// phase timestamps (clock64) of CTA 0, per line: [0] MMA warp got B, [1] MMA warp issued the
-// line, [3] epilogue got the accumulator, [4] epilogue released B, [5] epilogue finished the
-// tail rows, [6] epilogue issued the next input's loads
-__device__ long long g_tc_trace[2 * 65 * 8];
-extern "C" int mstopo_debug_tc_trace(long long* out, int n) {
-  return (int)cudaMemcpyFromSymbol(out, g_tc_trace, sizeof(long long) * (size_t)n);
-}
-#define TC_TR(ls, f, v) \
-  do { if (blockIdx.x == 0 && (ls) < 130) g_tc_trace[(ls) * 8 + (f)] = (v); } while (0)
-#else
-#define TC_TR(ls, f, v) do { } while (0)
-#endif
 
 // Bytes of one packed line: KS K-steps of [hi tile | lo tile] (128 rows x 8 columns, core
 // matrices of 8 rows x 16 B: row groups 256 B apart, column halves 128 B apart) followed by
@@ -292,9 +287,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
       // drain: the last fill of every stage (and tail buffer) has landed before the CTA exits
       for (int st = 0; st < NST && st < ug; ++st) {
         const int last = (ug - 1 - st) / NST;   // index of the last fill of stage st
-        tc_wait(&full[st], last & 1, &s_abort, err);
+        tc_drain(&full[st], last & 1, err);
       }
-      for (int b = 0; b < 2 && b < tfills; ++b) tc_wait(&tfull[b], ((tfills - 1 - b) / 2) & 1, &s_abort, err);
+      for (int b = 0; b < 2 && b < tfills; ++b) tc_drain(&tfull[b], ((tfills - 1 - b) / 2) & 1, err);
     }
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA issue
@@ -307,7 +302,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
       bool issued = false;
       for (int ls = 0; ls < 2 * NL; ++ls) {
         if (!tc_wait(&bready, ls & 1, &s_abort, err)) break;
-        TC_TR(ls, 0, clock64());
         tc_fence_after();
         bool ok = true;
         for (int u = 0; u < nunits; ++u, ++ug) {
@@ -330,11 +324,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
         }
         if (!ok) break;
         tc_commit(&ldone);
-        TC_TR(ls, 1, clock64());
       }
       if (issued) {   // drain: every MMA this thread issued has completed
         tc_commit(&fin);
-        tc_wait(&fin, 0, &s_abort, err);
+        tc_drain(&fin, 0, err);
       }
     }
   } else {
@@ -426,7 +419,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
         yt = acc;
         mbar_arrive(&tempty[b]);
       }
-      if (i == 0) TC_TR(ls, 5, clock64());
       // (b) next line's input (not for the first backward line: that is this line's result)
       if (nxt < 2 * NL && nxt != NL) {
         load_input(nxt, i, pf);
@@ -434,10 +426,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
       }
       // (c) accumulator of this line
       {
-        if (i == 0) TC_TR(ls, 6, clock64());
         const bool ok = tc_wait_warp(&ldone, ls & 1, &s_abort, err);
         if (epi_sync_or(!ok)) { abort = true; break; }
-        if (i == 0) TC_TR(ls, 3, clock64());
       }
       tc_fence_after();
       {
@@ -504,7 +494,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_patch_solve_tc(
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&bready);
-        if (i == 0) TC_TR(ls, 4, clock64());
       }
     }
   }
@@ -563,7 +552,7 @@ static cudaError_t launch_tc(mstopo_handle* h, const float* r, int sys0, int nsy
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     sms = n;
   }
-  const bool deep = ng <= sms || getenv("MSTOPO_TC_DEEP") != nullptr;
+  const bool deep = ng <= sms;
   return deep ? launch_tc_k<Q, TC_NST_DEEP>(h, r, sys0, g0, ng, Xg)
               : launch_tc_k<Q, TC_NST>(h, r, sys0, g0, ng, Xg);
 }

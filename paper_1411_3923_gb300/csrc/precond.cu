@@ -3,10 +3,12 @@
 //
 // Build (once per design):
 //   1. agglomerate de-duplication (Sec. 2.4.1): every agglomerate omega_i (the 2H x 2H
-//      elements around coarse node y_i, clipped by the mesh) is hashed over its moduli and
-//      its Dirichlet mask; agglomerates with equal hashes share one "type" and therefore one
-//      eigenbasis and one patch factor.  The paper observes three unique agglomerates for a
-//      periodic double-clamped beam; the hash generalises that to any design.
+//      elements around coarse node y_i, clipped by the mesh) is hashed over its moduli, its
+//      Dirichlet mask and which of its four box sides lie inside the mesh (those form the
+//      artificial boundary of its patch); agglomerates with equal hashes whose boxes then
+//      compare equal entry by entry share one "type" and therefore one eigenbasis and one
+//      patch factor.  The paper observes three unique agglomerates for a periodic
+//      double-clamped beam; the key generalises that to any design.
 //   2. per type, the agglomerate's Neumann matrix K_w (its own elements only, physical
 //      Dirichlet DOFs kept) is assembled block-tridiagonally by node rows; K_w + s diag(K_w)
 //      is factorised (FP64) and block subspace iteration with Rayleigh-Ritz finds the
@@ -57,9 +59,18 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// Artificial sides of agglomerate (I, J)'s box: bit 0 left, 1 right, 2 bottom, 3 top, set
+// when that side lies strictly inside the mesh (a side on or beyond the mesh edge keeps the
+// physical conditions).  Two boxes with equal moduli and masks but different sides have
+// different patch matrices.
+__host__ __device__ __forceinline__ int agg_sides(int I, int J, int H, int nelx, int nely) {
+  const int ox = (I - 1) * H, oy = (J - 1) * H;
+  return (ox > 0 ? 1 : 0) | (ox + 2 * H < nelx ? 2 : 0) | (oy > 0 ? 4 : 0) | (oy + 2 * H < nely ? 8 : 0);
+}
+
 // Hash of the moduli of realisation `salt` over the agglomerate (XOR-accumulated over the
 // realisations, so equal hashes mean equal boxes in every realisation) and, once
-// (with_mask), of its Dirichlet mask.
+// (with_mask), of its Dirichlet mask and its artificial sides.
 __global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restrict__ nmask,
                            int nelx, int nely, int H, int ncx, int salt, int with_mask,
                            unsigned long long* __restrict__ hash) {
@@ -69,6 +80,11 @@ __global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restri
   const int ne = 2 * H, nn = 2 * H + 1;
   const unsigned long long sk = mix64(0x5BD1E995ull + (unsigned long long)salt);
   unsigned long long h1 = 0, h2 = 0;
+  if (with_mask && threadIdx.x == 0) {
+    const unsigned long long sd = (unsigned long long)agg_sides(I, J, H, nelx, nely);
+    h1 ^= mix64((sd + 0x3C6EF372ull) ^ 0xA54FF53A5F1D36F1ull);
+    h2 ^= mix64(sd * 0x510E527FADE682D1ull + 0x9B05688C2B3E6C1Full);
+  }
   for (int t = threadIdx.x; t < ne * ne; t += blockDim.x) {
     int ex = ox + t % ne, ey = oy + t / ne;
     unsigned long long v = 0xFFFFFFFFFFFFFFFFull;
@@ -86,6 +102,46 @@ __global__ void k_hash_agg(const double* __restrict__ E, const uint8_t* __restri
   }
   atomicXor(&hash[2 * i], h1);
   atomicXor(&hash[2 * i + 1], h2);
+}
+
+// Entry-by-entry check of a hash match: agglomerate i against the representative rep of its
+// type, over the moduli of every realisation (bit patterns, and which elements lie inside
+// the mesh), the Dirichlet mask of the box nodes and the artificial sides.  bad[i] = 1 on
+// any difference (a hash collision); the host then gives i a type of its own.
+__global__ void k_verify_agg(const double* __restrict__ E, long long e_stride, int nsys,
+                             const uint8_t* __restrict__ nmask, int nelx, int nely, int H,
+                             int ncx, const int* __restrict__ type_of,
+                             const int* __restrict__ rep_of_type, int* __restrict__ bad) {
+  const int i = blockIdx.x;
+  const int ia = rep_of_type[type_of[i]];
+  if (ia == i) {
+    if (threadIdx.x == 0) bad[i] = 0;
+    return;
+  }
+  const int I = i % (ncx + 1), J = i / (ncx + 1);
+  const int Ia = ia % (ncx + 1), Ja = ia / (ncx + 1);
+  const int ox = (I - 1) * H, oy = (J - 1) * H, oxa = (Ia - 1) * H, oya = (Ja - 1) * H;
+  const int ne = 2 * H, nn = 2 * H + 1;
+  int diff = agg_sides(I, J, H, nelx, nely) != agg_sides(Ia, Ja, H, nelx, nely);
+  for (int t = threadIdx.x; !diff && t < ne * ne; t += blockDim.x) {
+    const int ex = ox + t % ne, ey = oy + t / ne, fx = oxa + t % ne, fy = oya + t / ne;
+    const bool in1 = ex >= 0 && ex < nelx && ey >= 0 && ey < nely;
+    const bool in2 = fx >= 0 && fx < nelx && fy >= 0 && fy < nely;
+    if (in1 != in2) { diff = 1; break; }
+    if (!in1) continue;
+    for (int k = 0; k < nsys; ++k)
+      if (__double_as_longlong(E[k * e_stride + (long long)ey * nelx + ex]) !=
+          __double_as_longlong(E[k * e_stride + (long long)fy * nelx + fx])) { diff = 1; break; }
+  }
+  for (int t = threadIdx.x; !diff && t < nn * nn; t += blockDim.x) {
+    const int x = ox + t % nn, y = oy + t / nn, xa = oxa + t % nn, ya = oya + t / nn;
+    const bool in1 = x >= 0 && x <= nelx && y >= 0 && y <= nely;
+    const bool in2 = xa >= 0 && xa <= nelx && ya >= 0 && ya <= nely;
+    if (in1 != in2) { diff = 1; break; }
+    if (in1 && nmask[(long long)y * (nelx + 1) + x] != nmask[(long long)ya * (nelx + 1) + xa]) diff = 1;
+  }
+  diff = __syncthreads_or(diff);
+  if (threadIdx.x == 0) bad[i] = diff ? 1 : 0;
 }
 
 // ----------------------------------------------------------------------------- assembly
@@ -1216,12 +1272,35 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       pc.h_type_of_agg[i] = it->second;
     }
   }
-  const int T = pc.n_types = (int)pc.h_rep_agg.size();
   int* d_rep;
-  CKB(cudaMalloc(&d_rep, T * sizeof(int)));
-  CKB(cudaMemcpyAsync(d_rep, pc.h_rep_agg.data(), T * sizeof(int), cudaMemcpyHostToDevice, s));
+  CKB(cudaMalloc(&d_rep, pc.Nc * sizeof(int)));
+  CKB(cudaMemcpyAsync(d_rep, pc.h_rep_agg.data(), pc.h_rep_agg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CKB(cudaMalloc(&pc.d_type_of_agg, pc.Nc * sizeof(int)));
   CKB(cudaMemcpyAsync(pc.d_type_of_agg, pc.h_type_of_agg.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  {
+    // a hash match is trusted only after the boxes compare equal entry by entry
+    int* d_bad;
+    CKB(cudaMalloc(&d_bad, pc.Nc * sizeof(int)));
+    note_launch(), k_verify_agg<<<pc.Nc, PC_THREADS, 0, s>>>(h->d_E64, h->n_el, nsv, h->d_nmask, h->nelx,
+                                                             h->nely, H, pc.ncx, pc.d_type_of_agg, d_rep, d_bad);
+    CKB(cudaGetLastError());
+    std::vector<int> bad(pc.Nc);
+    CKB(cudaMemcpyAsync(bad.data(), d_bad, pc.Nc * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(d_bad);
+    bool split = false;
+    for (int i = 0; i < pc.Nc; ++i)
+      if (bad[i]) {
+        pc.h_type_of_agg[i] = (int)pc.h_rep_agg.size();
+        pc.h_rep_agg.push_back(i);
+        split = true;
+      }
+    if (split) {
+      CKB(cudaMemcpyAsync(d_rep, pc.h_rep_agg.data(), pc.h_rep_agg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      CKB(cudaMemcpyAsync(pc.d_type_of_agg, pc.h_type_of_agg.data(), pc.Nc * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+  }
+  const int T = pc.n_types = (int)pc.h_rep_agg.size();
   CKB(cudaEventRecord(ev[1], s));
 
   // 2. agglomerate (Neumann, for the eigenproblem) and patch (artificial boundary Dirichlet)

@@ -35,7 +35,8 @@ class _Problem(C.Structure):
                 ("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("local_shift", C.c_double), ("stream", C.c_void_p),
                 ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32),
-                ("rebuild_ratio", C.c_double), ("preconditioner", C.c_int32)]
+                ("rebuild_ratio", C.c_double), ("preconditioner", C.c_int32),
+                ("patch_kernel", C.c_int32), ("exec_flags", C.c_int32)]
 
 
 class _BuildInfo(C.Structure):
@@ -54,6 +55,8 @@ class _Stats(C.Structure):
 
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
 PRECONDITIONERS = {"additive": 0, "sgs": 1}   # mstopo_preconditioner
+PATCH_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}   # mstopo_patch_kernel
+EXEC_NO_GRAPHS, EXEC_NO_SIDE_STREAM = 1, 2   # mstopo_problem.exec_flags bits
 
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
 
@@ -139,7 +142,10 @@ class Problem:
     overlapping exact patch solves) or "sgs" (the paper's own, Sec. 2.4.2: a symmetric
     Gauss-Seidel sweep, the coarse correction, a second sweep, applied multiplicatively).
     ``coarse_solver``: "auto", "dense" or "blocktri" for K_c u_c = r_c.
-    ``precision``: "mixed" (FP64 outer solve, FP32 inner arithmetic) or "fp64"."""
+    ``precision``: "mixed" (FP64 outer solve, FP32 inner arithmetic) or "fp64".
+    ``patch_kernel``: "auto", "cuda_cores" or "tensor_cores" for the FP32 patch solves.
+    ``graphs`` / ``side_stream``: False runs the flexible CG without CUDA graphs / the
+    preconditioner's coarse chain on the main stream."""
 
     def __init__(self, nelx: int, nely: int, fixed: np.ndarray, *, nu: float = 0.3,
                  E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
@@ -147,7 +153,8 @@ class Problem:
                  tol: float = 1e-8, max_iter: int = 2000, local_shift: float = 0.0,
                  stream: Optional[int] = None, coarse_solver: str = "auto",
                  reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0,
-                 preconditioner: str = "additive"):
+                 preconditioner: str = "additive", patch_kernel: str = "auto",
+                 graphs: bool = True, side_stream: bool = True):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
@@ -156,7 +163,8 @@ class Problem:
                      lambda_thresh, MIXED if precision == "mixed" else FP64, tol, max_iter,
                      local_shift, stream, COARSE_SOLVERS[coarse_solver],
                      1 if reuse_preconditioner else 0, rebuild_ratio,
-                     PRECONDITIONERS[preconditioner])
+                     PRECONDITIONERS[preconditioner], PATCH_KERNELS[patch_kernel],
+                     (0 if graphs else EXEC_NO_GRAPHS) | (0 if side_stream else EXEC_NO_SIDE_STREAM))
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:

@@ -51,3 +51,6 @@ def test_noalloc_rejects_meshes_above_its_fixed_capacity():
     dummy = ctypes.c_void_p(1)   # never dereferenced: the size check comes first
     st = lib.mstopo_apply_K_f32_noalloc(dummy, dummy, dummy, dummy, 2048, 1024, 0.3, None)
     assert st == 1   # MSTOPO_INVALID_ARG: 2*2049*1025 DOFs > 2^22
+    # the largest int32 sizes: the DOF count is formed in 64 bits and rejected, not wrapped
+    st = lib.mstopo_apply_K_f32_noalloc(dummy, dummy, dummy, dummy, 2**31 - 1, 2**31 - 1, 0.3, None)
+    assert st == 1
