@@ -99,57 +99,84 @@ def local_eigenpairs(Kw: sp.spmatrix, k: int, dense_limit: int = 900):
 
 
 class TwoLevel:
-    """The spectral coarse space and the additive two-level preconditioner on free DOFs."""
+    """The spectral coarse space and the additive two-level preconditioner on free DOFs.
+
+    basis: another TwoLevel whose coarse basis (agglomerates, eigenvectors, R_c) is taken as
+    it is, while K_c = R_c K R_c^T and the patch matrices come from E_neutral.  This is the
+    robust formulation's shared preconditioner (Sec. 5.3): the basis of the dilated design
+    serves every realisation, each realisation keeping its own operator K.
+
+    Identical local matrices have identical eigenpairs and factors, so each distinct
+    agglomerate matrix is eigen-solved once and each distinct patch matrix factorised once
+    (the unique agglomerates of a periodic microstructure, Sec. 2.4.1); the key is the
+    matrix itself (its CSR arrays, byte for byte)."""
 
     def __init__(self, prob: fem.Problem, E_neutral: np.ndarray, H: int, n_eig: int,
                  lam_thresh: float | None = None, with_patches: bool = True,
-                 dense_limit: int = 900):
+                 dense_limit: int = 900, basis: "TwoLevel | None" = None):
         g = prob.grid
         assert g.nelx % H == 0 and g.nely % H == 0, "mesh must be a whole number of coarse cells"
         self.prob, self.H = prob, H
         self.ncx, self.ncy = g.nelx // H, g.nely // H
         self.K = prob.free_matrix(E_neutral)
-        n_free = prob.free.size
-        pos = -np.ones(g.n_dof, dtype=np.int64)
-        pos[prob.free] = np.arange(n_free)
-        self.aggs, self.eigvals = [], []
-        cols, rows, vals = [], [], []
-        patch_dofs = []
-        t = 0
-        for J in range(self.ncy + 1):
-            for I in range(self.ncx + 1):
-                a = Agglomerate(I, J, H, g.nelx, g.nely)
-                gd = a.global_dofs(g)
-                keep = ~prob.fixed[gd]
-                Kw = a.local_stiffness(E_neutral, prob.K0)[keep][:, keep]
-                lam, psi = local_eigenpairs(Kw, n_eig, dense_limit)
-                if lam_thresh is not None:
-                    m = max(1, int(np.sum(lam < lam_thresh)))
-                    lam, psi = lam[:m], psi[:, :m]
-                chi = np.repeat(a.chi(H), 2)[keep]
-                phi = chi[:, None] * psi
-                fr = pos[gd[keep]]
-                for j in range(phi.shape[1]):
-                    nz = phi[:, j] != 0.0
-                    rows.append(fr[nz])
-                    cols.append(np.full(int(nz.sum()), t))
-                    vals.append(phi[nz, j])
-                    t += 1
-                self.aggs.append(a)
-                self.eigvals.append(lam)
-                interior = ~np.repeat(a.artificial, 2)
-                patch_dofs.append(pos[gd[keep & interior]])
-        self.Nt = t
-        self.RcT = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                                 shape=(n_free, t)).tocsr()
+        if basis is not None:
+            assert basis.prob is prob and basis.H == H
+            self.aggs, self.eigvals, self.Nt = basis.aggs, basis.eigvals, basis.Nt
+            self.RcT, patch_dofs = basis.RcT, basis.patch_dofs
+        else:
+            n_free = prob.free.size
+            pos = -np.ones(g.n_dof, dtype=np.int64)
+            pos[prob.free] = np.arange(n_free)
+            self.aggs, self.eigvals = [], []
+            cols, rows, vals = [], [], []
+            patch_dofs = []
+            memo = {}
+            t = 0
+            for J in range(self.ncy + 1):
+                for I in range(self.ncx + 1):
+                    a = Agglomerate(I, J, H, g.nelx, g.nely)
+                    gd = a.global_dofs(g)
+                    keep = ~prob.fixed[gd]
+                    Kw = sp.csr_matrix(a.local_stiffness(E_neutral, prob.K0)[keep][:, keep])
+                    key = _matrix_key(Kw)
+                    if key not in memo:
+                        memo[key] = local_eigenpairs(Kw, n_eig, dense_limit)
+                    lam, psi = memo[key]
+                    if lam_thresh is not None:
+                        m = max(1, int(np.sum(lam < lam_thresh)))
+                        lam, psi = lam[:m], psi[:, :m]
+                    chi = np.repeat(a.chi(H), 2)[keep]
+                    phi = chi[:, None] * psi
+                    fr = pos[gd[keep]]
+                    for j in range(phi.shape[1]):
+                        nz = phi[:, j] != 0.0
+                        rows.append(fr[nz])
+                        cols.append(np.full(int(nz.sum()), t))
+                        vals.append(phi[nz, j])
+                        t += 1
+                    self.aggs.append(a)
+                    self.eigvals.append(lam)
+                    interior = ~np.repeat(a.artificial, 2)
+                    patch_dofs.append(pos[gd[keep & interior]])
+            self.Nt = t
+            self.RcT = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                     shape=(n_free, t)).tocsr()
         self.Kc = np.asarray((self.RcT.T @ (self.K @ self.RcT)).todense())
         self.Kc = 0.5 * (self.Kc + self.Kc.T)
         self.Kc_chol = sla.cho_factor(self.Kc, lower=True)
         self.patch_dofs = patch_dofs
-        self.patch_lu = []
+        # patch solves grouped by identical matrix: (factor, [n_patch_dofs x patches] indices)
+        self.patch_groups = []
         if with_patches:
+            Kr = sp.csr_matrix(self.K)
+            groups = {}
             for d in patch_dofs:
-                self.patch_lu.append(spla.splu(self.K[d][:, d].tocsc()))
+                Ki = sp.csr_matrix(Kr[d][:, d])
+                key = _matrix_key(Ki)
+                if key not in groups:
+                    groups[key] = (spla.splu(Ki.tocsc()), [])
+                groups[key][1].append(d)
+            self.patch_groups = [(lu, np.stack(ds, axis=1)) for lu, ds in groups.values()]
 
     # --- operators on free-DOF vectors ---------------------------------------------------
     def coarse(self, r: np.ndarray) -> np.ndarray:
@@ -157,14 +184,20 @@ class TwoLevel:
         return self.RcT @ sla.cho_solve(self.Kc_chol, self.RcT.T @ r)
 
     def local(self, r: np.ndarray) -> np.ndarray:
-        """sum_i R_i^T K_i^-1 R_i r."""
+        """sum_i R_i^T K_i^-1 R_i r (patches with the same matrix solved as one block of
+        right-hand sides)."""
         z = np.zeros_like(r)
-        for d, lu in zip(self.patch_dofs, self.patch_lu):
-            z[d] += lu.solve(r[d])
+        for lu, D in self.patch_groups:
+            np.add.at(z, D, lu.solve(r[D]))
         return z
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         return self.coarse(r) + self.local(r)
+
+
+def _matrix_key(A: sp.csr_matrix):
+    A.sort_indices()
+    return (A.shape, A.indptr.tobytes(), A.indices.tobytes(), A.data.tobytes())
 
 
 def pcg(K: sp.spmatrix, f: np.ndarray, Minv, tol: float = 1e-8, maxit: int = 1000, x0=None):

@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.
 
   design chain (filter -> projection per eta -> SIMP)
   -> state solves K(E_k) u_k = f   (sparse LU, or PCG with the two-level preconditioner
-     built once on the dilated realisation, i.e. the smallest eta, as Sec. 5.3 prescribes)
+     whose coarse basis comes from the dilated realisation, i.e. the smallest eta, as
+     Sec. 5.3 prescribes, and whose K_c and patch matrices are those of realisation k)
   -> compliances c_k = f^T u_k, robust objective and its gradient w.r.t. the design.
 """
 from __future__ import annotations
@@ -31,16 +32,22 @@ def run(wl, solver: str = "direct", kappa: float = 1.0, tol: float | None = None
     fw = chain.forward(wl.rho)
     tol = wl.tol if tol is None else tol
     us, its, res = [], [], []
-    if solver == "pcg" and precond is None:
-        ref = int(np.argmin(wl.etas))
-        precond = msfem.TwoLevel(prob, fw["E"][ref], wl.H, wl.n_eig)
+    precs = None
+    if solver == "pcg":
+        if precond is not None:   # one operator for every realisation (caller's choice)
+            precs = [precond] * len(fw["E"])
+        else:
+            ref = int(np.argmin(wl.etas))
+            basis = msfem.TwoLevel(prob, fw["E"][ref], wl.H, wl.n_eig)
+            precs = [basis if k == ref else msfem.TwoLevel(prob, E, wl.H, wl.n_eig, basis=basis)
+                     for k, E in enumerate(fw["E"])]
     f_or = grid.nodal_from_neutral(wl.force)
-    for E in fw["E"]:
+    for k, E in enumerate(fw["E"]):
         if solver == "direct":
             us.append(prob.solve_direct(E, wl.force))
         else:
             Kf = prob.free_matrix(E)
-            x, it, rr = msfem.pcg(Kf, f_or[prob.free], precond.apply, tol=tol)
+            x, it, rr = msfem.pcg(Kf, f_or[prob.free], precs[k].apply, tol=tol)
             u = np.zeros(grid.n_dof)
             u[prob.free] = x
             us.append(grid.nodal_to_neutral(u))

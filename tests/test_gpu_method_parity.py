@@ -107,10 +107,14 @@ def test_type_count_keys_on_artificial_sides(c2_copy):
     assert c.info["n_types"] == n == 25
 
 
-def test_full_size_bench_workload_type_count():
+def test_full_size_bench_workload_types_and_residual_certificate():
+    """The 1024x512 workload as the benchmark runs it (MIXED, tol 1e-8): the type count equals
+    the exact key's, and the oracle's assembled FP64 K certifies the returned u: the true
+    relative residual over the free DOFs is at most the tolerance (plus FP64 round-off of the
+    residual itself), and the library's compliance equals f^T u."""
     m = _gpu()
     wl = workloads.make("mbb_c2")
-    _, _, _, chain = pipeline.build(wl)
+    grid, K0, oprob, chain = pipeline.build(wl)
     E = chain.forward(wl.rho)["E"]
     prob = make_problem(m, wl, "mixed")
     prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
@@ -118,6 +122,14 @@ def test_full_size_bench_workload_type_count():
     n = exact_type_count(wl, E)
     print("1024x512 types", info["n_types"], "exact key", n)
     assert info["n_agglomerates"] == 561 and info["n_types"] == n
+    u, infos = prob.solve(cuda(wl.force), -1)
+    uf = grid.nodal_from_neutral(u[0].cpu().numpy())[oprob.free]
+    ff = grid.nodal_from_neutral(wl.force)[oprob.free]
+    rr = np.linalg.norm(ff - oprob.free_matrix(E[0]) @ uf) / np.linalg.norm(ff)
+    print("oracle residual", rr, "library", infos[0]["rel_residual"], "iterations", infos[0]["iterations"])
+    assert infos[0]["status"] == 0 and rr <= 1.01e-8
+    assert abs(rr - infos[0]["rel_residual"]) <= 1e-3 * rr
+    assert infos[0]["compliance"] == pytest.approx(float(ff @ uf), rel=1e-12)
 
 
 def test_patch_operator_at_H32_on_a_periodic_design(c2_copy):
@@ -204,3 +216,23 @@ def test_iteration_count_matches_oracle_pcg_on_c1_full_size(precision):
     print(precision, "C1 GPU iterations", it, "oracle", it_ref)
     assert infos[0]["status"] == 0
     assert abs(it - it_ref) <= max(1, int(np.ceil(0.1 * it_ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_three_realisation_iteration_counts_match_the_oracle(precision):
+    """The robust batch (Sec. 5.3): basis of the dilated realisation, K_c and patches per
+    realisation.  On a 192x256 copy of the 26.2M-DOF periodic workload each realisation needs
+    the oracle's PCG iteration count (within 10 %) and reaches its compliance."""
+    m = _gpu()
+    wl = workloads.make("mbb_c5", 16)
+    out = pipeline.run(wl, "pcg", tol=1e-8, with_grad=False)
+    prob = make_problem(m, wl, precision, tol=1e-8)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    _, infos = prob.solve(cuda(wl.force), -1)
+    its = [i["iterations"] for i in infos]
+    print(precision, "GPU iterations", its, "oracle", out["iterations"])
+    for it, it_ref, inf, c in zip(its, out["iterations"], infos, out["c"]):
+        assert inf["status"] == 0
+        assert abs(it - it_ref) <= max(1, int(np.ceil(0.1 * it_ref)))
+        assert inf["compliance"] == pytest.approx(c, rel=1e-7)
