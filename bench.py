@@ -42,8 +42,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one FP32 patch-solve launch on the 1024x512 workload, from an
 # ncu capture of `bench.py --only patch` (dram__bytes_read.sum + dram__bytes_write.sum of the
-# current kernel); None once the kernel changes
-PATCH_TRAFFIC_BYTES = 294.4e6 + 26.6e6
+# current kernel); None until the current kernel has been captured
+PATCH_TRAFFIC_BYTES = None
 
 
 def load_peaks():
@@ -321,14 +321,16 @@ def run_ours(args, rank: int, world: int):
     n_iter_total = sum(sum(p["iters"]) for p in per)
     # algorithmic work per launch
     nodes = (wl.nelx + 1) * (wl.nely + 1)
-    patch_flops = 6.0 * wl_N * nb * nb * n_agg * len(wl.etas)        # 2 sweeps x (Linv/2 + C) per column
+    # banded triangular-solve pair per patch: 4 n b flops, n = NL nb box DOFs, b = nb
+    patch_flops = 4.0 * (wl_N * nb) * nb * n_agg * len(wl.etas)
     mv_bytes = nodes * 8 * 2 + wl.nelx * wl.nely * 4 + nodes          # u, y (float2), E, mask
     cand = []
     if kern["patch_solve"]["launches"]:
         t = kern["patch_solve"]["ms"] / kern["patch_solve"]["launches"]
         ach = patch_flops / (t * 1e-3) / 1e12
         cand.append((kern["patch_solve"]["ms"], {
-            "kernel": "k_patch_solve<float>", "bound": "alu", "achieved": ach,
+            "kernel": "k_patch_tri<float>", "bound": "alu", "achieved": ach,
+            "work": "4 n b flops per patch (n = 65 x 130 box DOFs, b = 130), 561 patches",
             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
             "traffic": PATCH_TRAFFIC_BYTES, "traffic_unit": "B per launch (ncu)", "avg_launch_ms": t,
             "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz"}))

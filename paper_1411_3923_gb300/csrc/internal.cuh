@@ -138,20 +138,30 @@ struct Precond {
   int* d_type_of_agg = nullptr;     // [Nc]
   int* d_kept = nullptr;            // [n_types]
   int* d_coff = nullptr;            // [Nc+1] coarse-unknown offsets
-  // patch-solve work groups: [0] for the CUDA-core kernels (FP64, and FP32 when the tensor
-  // cores are off), [1] for the tensor-core FP32 kernel (PATCH_COLS patches per group)
-  PatchGroups pg[2];
+  // patch-solve work groups: [0] FP32 on the CUDA cores, [1] FP32 on the tensor cores
+  // (PATCH_COLS patches per group), [2] FP64 (at most 4 patches per group)
+  PatchGroups pg[3];
   int nsv = 0;                      // realisations with their own operators
-  // per-type patch factors (block tridiagonal by node rows of the (2H+1)^2 agglomerate box,
-  // artificial-boundary nodes Dirichlet): Linv [NP][nbP][nbP], C [NP-1][nbP][nbP]
+  // per-system patch matrices: block tridiagonal by node rows of the (2H+1)^2 agglomerate
+  // box, artificial-boundary nodes Dirichlet
   uint8_t* d_pfree = nullptr;       // [T][NP*nbP] free DOFs of the patch box
-  double* d_pLinv64 = nullptr; double* d_pC64 = nullptr;
-  float* d_pLinv32 = nullptr;  float* d_pC32 = nullptr;
-  // packed stage blocks for the cluster patch solve: [T][NL][4 ranks][2][rpc][nbs]
-  double* d_pf64 = nullptr; double* d_pb64 = nullptr;
-  float* d_pf32 = nullptr;  float* d_pb32 = nullptr;
-  int rpc = 0, nbs = 0;
-  // tensor-core FP32 patch solve (csrc/patch_tc.cu): TF32 hi/lo factor lines [T][2][NL][line]
+  // patch solves on the CUDA cores (csrc/patch_tri.cu): per (system, line) the packed
+  // lower-triangular Linv_k and the coupling block B_k, FP64 and FP32 [T*nsv][NL][line]
+  double* d_tri64 = nullptr;
+  float* d_tri32 = nullptr;
+  // patch solves on the CUDA cores from the packed triangular factors (csrc/patch_tri.cu)
+bool patch_tri_assignment_ok(int nb);
+// right-hand-side columns of a CUDA-core patch-solve CTA for groups of up to P patches
+inline int patch_tri_cols(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : 16); }
+long long patch_tri_line_elems(int nb);
+cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
+                           double* out64, float* out32, cudaStream_t s);
+cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
+                                int nsys, float* Xg);
+cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const double* r, int sys0,
+                                int nsys, double* Xg);
+
+// tensor-core FP32 patch solve (csrc/patch_tc.cu): TF32 hi/lo factor lines [T][2][NL][line]
   unsigned char* d_ptc = nullptr;
   long long tc_line_bytes = 0;
   int patch_tc = 0;
@@ -283,6 +293,18 @@ cudaError_t smem_limit_max() {
   }();
   return once;
 }
+
+// patch solves on the CUDA cores from the packed triangular factors (csrc/patch_tri.cu)
+bool patch_tri_assignment_ok(int nb);
+// right-hand-side columns of a CUDA-core patch-solve CTA for groups of up to P patches
+inline int patch_tri_cols(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : 16); }
+long long patch_tri_line_elems(int nb);
+cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
+                           double* out64, float* out32, cudaStream_t s);
+cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
+                                int nsys, float* Xg);
+cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const double* r, int sys0,
+                                int nsys, double* Xg);
 
 // tensor-core FP32 patch solve (csrc/patch_tc.cu)
 long long patch_tc_line_bytes(int nb);

@@ -40,11 +40,8 @@ namespace cg = cooperative_groups;
 #define PC_THREADS 256
 #define SOLVE_THREADS 320   // 160 rows x 2 threads per pass covers nb = 2(2H+1) up to H = 39
 #define EIG_CL 4            // CTAs per agglomerate type in the eigen-solve (subspace columns split)
-#define PATCH_HALVES 2      // row halves of every line in the patch solve
-#define PATCH_MAX_HP 33     // row pairs per half-stage the patch solve covers: H <= 32
 #define PATCH_COLS 16       // right-hand-side columns per CTA (patches x systems), at most
-#define PATCH_GROUP 4       // patches per CTA
-#define PATCH_PF 8          // prefetched input values per thread (nb * R <= 8 x threads)
+#define PATCH_COLS_F64 4    // the same for the FP64 patch solves
 #define EIG_MAX_SWEEPS 80
 #define EIG_TOL 1e-7
 #define EIG_SHIFT 1e-5
@@ -828,260 +825,6 @@ __global__ void k_coarse_gemv(const double* __restrict__ Kinv, const double* __r
   if (lane == 0) uc[(long long)s * Nt + warp] = acc;
 }
 
-// Patch solves, one CTA per group of up to P patches of one type (all systems: R = 4Q
-// right-hand-side columns, zero padded).  The block-tridiagonal factor is applied as
-//   forward   y_k = Linv_k b_k - W_k y_{k-1}        (W_k = Linv_k C_{k-1})
-//   backward  x_k = Linv_k^T y_k - V_k x_{k+1}     (V_k = Linv_k^T C_k^T)
-// so each line is one fused product of two known vectors.  The rows of every line are
-// processed in two halves; each half-stage block [A rows | B rows] (A = Linv_k or Linv_k^T,
-// B = W_k or V_k, hrows rows of stride nbs) is one bulk copy, double-buffered (FP32) so the
-// next half loads while the current one is used.  S threads share a row (float4 reads of
-// the row and of the vectors, shuffle reduction).  The right-hand sides are read straight
-// from r at each forward line; y_k is kept in the work buffer for the backward sweep, which
-// overwrites line k with x_k.  Work buffer Xg: [group][line][nb][R] (y), then [group][line][R][nb] (x).
-// R consecutive values (R a multiple of 4, 16-byte aligned) from shared memory
-template <typename T, int R>
-__device__ __forceinline__ void load_vec(const T* p, T* v) {
-  if (sizeof(T) == 4) {
-#pragma unroll
-    for (int j = 0; j < R; j += 4) {
-      const float4 w = *reinterpret_cast<const float4*>(p + j);
-      v[j] = w.x; v[j + 1] = w.y; v[j + 2] = w.z; v[j + 3] = w.w;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < R; j += 2) {
-      const double2 w = *reinterpret_cast<const double2*>(p + j);
-      v[j] = w.x; v[j + 1] = w.y;
-    }
-  }
-}
-
-// Groups g0 + blockIdx.x; a group is up to R agglomerates of one type in one realisation
-// (column p = agglomerate p of the group); its right-hand sides come from system
-// grp_sys[g] - sys0 of r.  The R columns are split over patch_cg(Q) thread groups of
-// patch_threads(Q) threads (patch_cpt(Q) columns each), which multiplies the warps that hide
-// the shared-memory latency of the row products.
-__host__ __device__ constexpr int patch_cpt(int Q) { return Q == 4 ? 8 : 4; }
-__host__ __device__ constexpr int patch_cg(int Q) { return 4 * Q / patch_cpt(Q); }
-// threads sharing one row pair (16 with a 4-deeper reduction was slower at four columns);
-// threads of one column group (a warp multiple)
-__host__ __device__ constexpr int patch_s(int) { return 8; }
-__host__ __device__ constexpr int patch_threads(int Q) {
-  return (PATCH_MAX_HP * patch_s(Q) + 31) / 32 * 32;
-}
-// Row stride of the right-hand-side vectors in shared memory: the 8 lanes that share a row
-// pair read 8 consecutive rows with 16-byte loads, which are bank-conflict free when a row
-// is an odd number of 16-byte chunks.
-template <typename T>
-__host__ __device__ constexpr int patch_rs(int R) {
-  return sizeof(T) == 4 ? ((R / 4) % 2 == 0 ? R + 4 : R) : R + 2;
-}
-
-template <typename T, int Q, int NBUF>
-__global__ void __launch_bounds__(patch_threads(Q) * patch_cg(Q)) k_patch_solve_f(
-    const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
-    int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
-    const int* __restrict__ grp_first, const int* __restrict__ grp_count,
-    const int* __restrict__ perm, const uint8_t* __restrict__ pfree,
-    const T* __restrict__ fwd, const T* __restrict__ bwd, int nbs, int hrows,
-    T* __restrict__ Xg, int* __restrict__ err) {
-  constexpr int R = 4 * Q;
-  constexpr int RS = patch_rs<T>(R);
-  constexpr int S = patch_s(Q);
-  constexpr int GT = patch_threads(Q);
-  __shared__ __align__(8) uint64_t bars[NBUF];
-  __shared__ int s_abort;
-  __shared__ int s_node[PATCH_COLS];   // patch origin per column block: (I-1)H, (J-1)H packed
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int g = g0 + blockIdx.x;
-  const int type = grp_type[g], first = grp_first[g], cnt = grp_count[g];
-  const T* rs = r + (long long)(grp_sys[g] - sys0) * stride;
-  const int N = 2 * H + 1, nb = 2 * N, NL = N;
-  const long long blk = 2LL * hrows * nbs;
-  const uint32_t bytes = (uint32_t)(blk * sizeof(T));
-  T* stg = reinterpret_cast<T*>(smraw);                 // [NBUF][2][hrows][nbs]
-  static_assert(NBUF >= 1 && NBUF <= 3, "stage buffers");
-  T* vb = stg + NBUF * blk;                             // [nbs][RS] input b_k or y_k
-  T* prev = vb + (long long)nbs * RS;                   // [nbs][RS] y_{k-1} or x_{k+1}
-  T* cur = prev + (long long)nbs * RS;                  // [nbs][RS] this line's result
-  const uint8_t* fr = pfree + (long long)type * N * nb;
-  T* X = Xg + (long long)g * NL * R * nb;
-  if (threadIdx.x < PATCH_COLS) {
-    const int p = threadIdx.x;
-    int v = -1;
-    if (p < cnt) {
-      const int ia = perm[first + p];
-      v = ia;
-    }
-    s_node[p] = v;
-  }
-  if (threadIdx.x == 0) {
-    s_abort = 0;
-    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
-  }
-  __syncthreads();
-  const int nseq = 4 * NL;   // 2 directions x NL lines x 2 halves
-  auto src = [&](int m) -> const T* {
-    const int line = m >> 1, half = m & 1;
-    if (line < NL) return fwd + (((long long)type * NL + line) * 2 + half) * blk;
-    const int k = NL - 1 - (line - NL);
-    return bwd + (((long long)type * NL + k) * 2 + half) * blk;
-  };
-  if (threadIdx.x == 0)
-    for (int b = 0; b < NBUF && b < nseq; ++b) {
-      mbar_expect_tx(&bars[b], bytes);
-      bulk_g2s(stg + b * blk, src(b), bytes, &bars[b]);
-    }
-  uint32_t phase[NBUF];
-#pragma unroll
-  for (int b = 0; b < NBUF; ++b) phase[b] = 0u;
-  // thread roles: column group cgi (columns j0 .. j0 + CPT), a pair of rows (rl, rl + hp)
-  // of the half block, reduction part pp of S
-  constexpr int CPT = patch_cpt(Q);
-  const int cgi = threadIdx.x / GT, t = threadIdx.x % GT;
-  const int j0 = cgi * CPT;
-  const int pp = t % S, rl = t / S;
-  const int hp = (hrows + 1) >> 1;
-  // zero the padding rows of the vectors once (nb..nbs-1) so the inner loops need no bounds
-  for (int q = nb * RS + threadIdx.x; q < nbs * RS; q += blockDim.x) {
-    vb[q] = T(0);
-    prev[q] = T(0);
-    cur[q] = T(0);
-  }
-  // The input vector of every line is loaded into registers while the previous line computes
-  // (PATCH_PF values per thread): forward lines gather r, backward lines read y_k from the
-  // work buffer; the first backward line takes y_{NL-1} from shared memory (just computed).
-  T pf[PATCH_PF];
-  auto load_line = [&](int ls) {
-    const bool fw = ls < NL;
-    const int k = fw ? ls : NL - 1 - (ls - NL);
-#pragma unroll
-    for (int i = 0; i < PATCH_PF; ++i) {
-      const int q = threadIdx.x + i * blockDim.x;
-      T v = T(0);
-      if (q < nb * R) {
-        if (fw) {
-          const int c = q / R, p = q % R;
-          if (p < cnt && fr[(long long)k * nb + c]) {
-            const int ia = s_node[p];
-            const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-            const int x = (I - 1) * H + (c >> 1), y = (J - 1) * H + k;
-            if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
-              v = rs[2 * ((long long)y * (nelx + 1) + x) + (c & 1)];
-          }
-        } else {
-          v = X[(long long)k * nb * R + q];
-        }
-      }
-      pf[i] = v;
-    }
-  };
-  load_line(0);
-  int m = 0;
-  for (int ls = 0; ls < 2 * NL; ++ls) {
-    const bool fw = ls < NL;
-    const int k = fw ? ls : NL - 1 - (ls - NL);
-    const bool has_prev = fw ? (k > 0) : (k < NL - 1);
-    // input vector of the line
-    if (ls == NL) {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) vb[(q / R) * RS + q % R] = prev[(q / R) * RS + q % R];
-    } else {
-#pragma unroll
-      for (int i = 0; i < PATCH_PF; ++i) {
-        const int q = threadIdx.x + i * blockDim.x;
-        if (q < nb * R) vb[(q / R) * RS + q % R] = pf[i];
-      }
-    }
-    __syncthreads();
-    if (ls + 1 < 2 * NL && ls + 1 != NL) load_line(ls + 1);
-    for (int half = 0; half < 2; ++half, ++m) {
-      const int b = m % NBUF;
-      if (threadIdx.x == 0 && !s_abort && !mbar_wait(&bars[b], phase[b])) {
-        s_abort = 1;
-        atomicExch(err, (int)MSTOPO_TIMEOUT);
-      }
-      phase[b] ^= 1u;
-      __syncthreads();
-      const T* A = stg + b * blk;
-      const T* Bm = A + (long long)hrows * nbs;
-      const int ra = rl, rb = rl + hp;                  // local rows of the pair
-      const bool va = ra < hp && half * hrows + ra < nb;
-      const bool vbr = va && rb < hrows && half * hrows + rb < nb;
-      const int ia = half * hrows + ra, ib = half * hrows + rb;
-      T acc0[CPT], acc1[CPT];
-#pragma unroll
-      for (int j = 0; j < CPT; ++j) { acc0[j] = T(0); acc1[j] = T(0); }
-      if (va) {
-        // lanes of a row pair take every S-th column (conflict-free shared loads of both the
-        // matrix rows and the vectors); the factor is zero outside each row's triangle
-        const T* Ar0 = A + (long long)ra * nbs;
-        const T* Ar1 = A + (long long)(vbr ? rb : ra) * nbs;
-        const int hi = vbr ? ib : ia;
-        const int c0 = fw ? 0 : ia, c1 = fw ? hi + 1 : nb;
-#pragma unroll 4
-        for (int c = c0 + pp; c < c1; c += S) {
-          const T a0 = Ar0[c], a1 = Ar1[c];
-          T v[CPT];
-          load_vec<T, CPT>(vb + c * RS + j0, v);
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) {
-            acc0[j] = fma(a0, v[j], acc0[j]);
-            acc1[j] = fma(a1, v[j], acc1[j]);
-          }
-        }
-        if (has_prev) {
-          const T* Br0 = Bm + (long long)ra * nbs;
-          const T* Br1 = Bm + (long long)(vbr ? rb : ra) * nbs;
-#pragma unroll 4
-          for (int c = pp; c < nb; c += S) {
-            const T a0 = Br0[c], a1 = Br1[c];
-            T v[CPT];
-            load_vec<T, CPT>(prev + c * RS + j0, v);
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-              acc0[j] = fma(-a0, v[j], acc0[j]);
-              acc1[j] = fma(-a1, v[j], acc1[j]);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int o = 1; o < S; o <<= 1)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          acc0[j] += __shfl_xor_sync(0xffffffffu, acc0[j], o);
-          acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], o);
-        }
-      if (pp == 0) {
-        if (va) {
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) cur[ia * RS + j0 + j] = acc0[j];
-        }
-        if (vbr) {
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) cur[ib * RS + j0 + j] = acc1[j];
-        }
-      }
-      __syncthreads();   // block b consumed: refill it
-      if (threadIdx.x == 0 && !s_abort && m + NBUF < nseq) {
-        mbar_expect_tx(&bars[b], bytes);
-        bulk_g2s(stg + b * blk, src(m + NBUF), bytes, &bars[b]);
-      }
-    }
-    // publish the line: forward y_k -> work buffer [nb][R]; backward x_k -> [R][nb]
-    T* Xk = X + (long long)k * nb * R;
-    if (fw) {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q / R) * RS + q % R];
-    } else {
-      for (int q = threadIdx.x; q < nb * R; q += blockDim.x) Xk[q] = cur[(q % nb) * RS + q / nb];
-    }
-    // the result becomes the previous-line vector
-    T* tmp = prev; prev = cur; cur = tmp;
-    __syncthreads();
-  }
-}
-
 // z(node) = sum over the agglomerates whose box contains the node of
 //           chi_i psi_i uc_i  (coarse part)  +  patch solution of omega_i at the node.
 // One thread per node (2D grid: x fastest), arithmetic in T.
@@ -1163,35 +906,6 @@ __global__ void __launch_bounds__(PC_THREADS) k_patch_wv(const double* __restric
   }
 }
 
-// Solve-ready layout for the patch solve: per (type, line, row half) one contiguous stage
-// block of two row slices (rpc rows, row stride nbs, zero padded):
-// forward [Linv_k rows | W_k rows], backward [Linv_k^T rows | V_k rows].
-__global__ void k_patch_pack(const double* __restrict__ Linv, const double* __restrict__ W,
-                             const double* __restrict__ V, int nb, int NL, int rpc, int nbs,
-                             double* __restrict__ f64, double* __restrict__ b64,
-                             float* __restrict__ f32, float* __restrict__ b32) {
-  const int type = blockIdx.x, k = blockIdx.y, bw = blockIdx.z;
-  const long long nn = (long long)nb * nb;
-  const long long blk = 2LL * rpc * nbs;
-  const double* Lk = Linv + ((long long)type * NL + k) * nn;
-  const double* Mk = (bw ? V : W) + ((long long)type * NL + k) * nn;
-  for (long long t = threadIdx.x; t < (long long)PATCH_HALVES * blk; t += blockDim.x) {
-    const int rank = t / blk;
-    const long long u = t % blk;
-    const int half = u / ((long long)rpc * nbs);
-    const int r = (u / nbs) % rpc, c = u % nbs;
-    const int row = rank * rpc + r;
-    double v = 0.0;
-    if (row < nb && c < nb) {
-      if (half == 0) v = bw ? Lk[(long long)c * nb + row] : Lk[(long long)row * nb + c];
-      else v = Mk[(long long)row * nb + c];
-    }
-    const long long o = (((long long)type * NL + k) * PATCH_HALVES) * blk + t;
-    if (bw) { b64[o] = v; if (b32) b32[o] = (float)v; }
-    else { f64[o] = v; if (f32) f32[o] = (float)v; }
-  }
-}
-
 // ------------------------------------------------------------------------------ host side
 #define CKB(x)                                                                  \
   do {                                                                          \
@@ -1209,8 +923,8 @@ void precond_free(Precond& pc) {
   for (PatchGroups& G : pc.pg) {
     dfree(G.d_perm); dfree(G.d_type); dfree(G.d_first); dfree(G.d_count); dfree(G.d_sys); dfree(G.d_agg);
   }
-  dfree(pc.d_pfree); dfree(pc.d_pLinv64); dfree(pc.d_pC64); dfree(pc.d_pLinv32); dfree(pc.d_pC32);
-  dfree(pc.d_pf64); dfree(pc.d_pb64); dfree(pc.d_pf32); dfree(pc.d_pb32); dfree(pc.d_ptc);
+  dfree(pc.d_pfree);
+  dfree(pc.d_tri64); dfree(pc.d_tri32); dfree(pc.d_ptc);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
   dfree(pc.d_Kc); dfree(pc.d_Kcinv);
   dfree(pc.d_cLinv); dfree(pc.d_cLinvT); dfree(pc.d_cW); dfree(pc.d_cV);
@@ -1414,48 +1128,39 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const int P = std::max(1, std::min(PATCH_COLS, (pc.Nc * nsv + sms - 1) / std::max(sms, 1)));
-  const int Qp = (P + 3) / 4;
-  pc.rpc = (nbP + PATCH_HALVES - 1) / PATCH_HALVES;
-  if ((pc.rpc + 1) / 2 > PATCH_MAX_HP) {
+  if (!patch_tri_assignment_ok(nbP)) {
     h->err = "H > 32 is not supported by the patch solve";
     return MSTOPO_INVALID_ARG;
   }
-  // factor row stride: a multiple of 4 that puts the rows one warp reads in one shared load
-  // on disjoint banks: 4 row pairs x 8 lanes (stride = 8 mod 32 floats) or 2 row pairs x 16
-  // lanes (stride = 16 mod 32)
-  pc.nbs = (nbP + 3) / 4 * 4;
-  while (pc.nbs % 32 != (patch_s(Qp) == 16 ? 16 : 8)) pc.nbs += 4;
   if (!sgs) {
     const double* pLi = dLi + (size_t)T * NA * nnA;
-    const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
-    double *dW, *dV;
-    CKB(cudaMalloc(&dW, (size_t)TP * NP * nnP * 8));
-    CKB(cudaMalloc(&dV, (size_t)TP * NP * nnP * 8));
-    note_launch(), k_patch_wv<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
-    CKB(cudaGetLastError());
-    const size_t pk = (size_t)TP * NP * PATCH_HALVES * 2 * pc.rpc * pc.nbs;
-    CKB(cudaMalloc(&pc.d_pf64, pk * 8));
-    CKB(cudaMalloc(&pc.d_pb64, pk * 8));
-    // FP32: the tensor-core line pack, or the CUDA-core stage blocks
+    const double* pB = dB + (size_t)T * (NA - 1) * nnA;
+    // the CUDA-core patch solves stream Linv_k and B_k (FP64 always, FP32 unless the tensor
+    // cores take the FP32 patch solves)
     // The tensor-core kernel's line has a fixed MMA chain (68 tcgen05.mma whatever the number
     // of columns): it pays off with full 16-column groups and two CTAs per SM; on small
     // problems (a few patches per SM) the CUDA-core kernel's shorter line wins.
     pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 32LL * sms);
+    const size_t tl = (size_t)TP * NP * patch_tri_line_elems(nbP);
+    CKB(cudaMalloc(&pc.d_tri64, tl * 8));
+    if (!pc.patch_tc) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
+    CKB(patch_tri_pack(pLi, pB, TP, nbP, NP, pc.d_tri64, pc.d_tri32, s));
     if (pc.patch_tc) {
+      // tensor-core FP32 line pack: [Linv_k | -W_k], [Linv_k^T | -V_k]
+      const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
+      double *dW, *dV;
+      CKB(cudaMalloc(&dW, (size_t)TP * NP * nnP * 8));
+      CKB(cudaMalloc(&dV, (size_t)TP * NP * nnP * 8));
+      note_launch(), k_patch_wv<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
+      CKB(cudaGetLastError());
       pc.tc_line_bytes = patch_tc_line_bytes(nbP);
       CKB(cudaMalloc(&pc.d_ptc, (size_t)TP * 2 * NP * pc.tc_line_bytes));
       CKB(patch_tc_pack(pLi, dW, dV, TP, nbP, NP, pc.d_ptc, s));
-    } else {
-      CKB(cudaMalloc(&pc.d_pf32, pk * 4));
-      CKB(cudaMalloc(&pc.d_pb32, pk * 4));
+      CKB(cudaStreamSynchronize(s));
+      cudaFree(dW);
+      cudaFree(dV);
     }
-    note_launch(), k_patch_pack<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, dW, dV, nbP, NP, pc.rpc,
-                                                                    pc.nbs, pc.d_pf64, pc.d_pb64,
-                                                                    pc.d_pf32, pc.d_pb32);
-    CKB(cudaGetLastError());
     CKB(cudaStreamSynchronize(s));
-    cudaFree(dW);
-    cudaFree(dV);
   }
   cudaFree(dLi); cudaFree(dC); cudaFree(dS); cudaFree(dX); cudaFree(dY); cudaFree(dKY);
   cudaFree(dKX); cudaFree(dYsc); cudaFree(dGM); cudaFree(dres);
@@ -1631,9 +1336,10 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   CKB(cudaStreamSynchronize(s));
   if (!sgs) CKB(build_groups(pc.pg[0], P));
   if (!sgs && pc.patch_tc) CKB(build_groups(pc.pg[1], PATCH_COLS));
+  if (!sgs) CKB(build_groups(pc.pg[2], std::min(P, PATCH_COLS_F64)));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
-  const size_t xg = (size_t)std::max(pc.pg[0].n, pc.pg[1].n) * nP * PATCH_COLS;
+  const size_t xg = (size_t)std::max({pc.pg[0].n, pc.pg[1].n, pc.pg[2].n}) * nP * PATCH_COLS;
   if (xg) {
     CKB(cudaMalloc(&pc.d_zp32, xg * 4));
     CKB(cudaMalloc(&pc.d_zp64, xg * 8));
@@ -1665,33 +1371,9 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   return MSTOPO_OK;
 }
 
-template <typename T, int Q>
-static cudaError_t launch_patch(mstopo_handle* h, const T* r, int sys0, int nsys, const T* fwd,
-                                const T* bwd, T* Xg) {
-  Precond& pc = h->pc;
-  const int nb = pc.nbP, R = 4 * Q;
-  // stage buffers: FP32 two (the next half-stage loads while one is used), FP64 one
-  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
-  const long long blk = 2LL * pc.rpc * pc.nbs;
-  const size_t sm = (size_t)(NBUF * blk + 3LL * pc.nbs * patch_rs<T>(R)) * sizeof(T);
-  (void)nb;
-  {
-    cudaError_t e = smem_limit_max<k_patch_solve_f<T, Q, NBUF>>();
-    if (e != cudaSuccess) return e;
-  }
-  if (sm > 225 * 1024) return cudaErrorInvalidConfiguration;
-  const PatchGroups& G = pc.pg[0];
-  const int g0 = G.h_begin[sys0], ng = G.h_begin[sys0 + nsys] - g0;
-  note_launch(), k_patch_solve_f<T, Q, NBUF><<<ng, patch_threads(Q) * patch_cg(Q), sm, h->s>>>(
-      r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, G.d_type, G.d_sys,
-      G.d_first, G.d_count, G.d_perm, pc.d_pfree, fwd, bwd, pc.nbs, pc.rpc, Xg,
-      h->d_flag + 1);
-  return cudaGetLastError();
-}
-
 template <typename T>
 static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int nsys, int part,
-                              const T* psi, const T* fwd, const T* bwd, T* Xg) {
+                              const T* psi, T* Xg) {
   Precond& pc = h->pc;
   cudaStream_t s = h->s;
   const long long n = h->n_dof;
@@ -1737,20 +1419,17 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
   }
   bool use_tc = false;
   if constexpr (sizeof(T) == 4) use_tc = pc.patch_tc != 0;
-  const PatchGroups& G = pc.pg[use_tc ? 1 : 0];
+  const PatchGroups& G = pc.pg[sizeof(T) == 8 ? 2 : (use_tc ? 1 : 0)];
   int Rcols = 4;
   if (part != 1) {
     const int Q = (G.P + 3) / 4;
-    Rcols = 4 * Q;
+    Rcols = use_tc ? 4 * Q : patch_tri_cols(G.P);
     cudaEvent_t pa = prof_begin(h->prof, s);
     cudaError_t e;
-    if (use_tc) {
-      if constexpr (sizeof(T) == 4) e = patch_tc_solve(h, Q, r, sys0, nsys, Xg);
-    } else switch (Q) {
-      case 1: e = launch_patch<T, 1>(h, r, sys0, nsys, fwd, bwd, Xg); break;
-      case 2: e = launch_patch<T, 2>(h, r, sys0, nsys, fwd, bwd, Xg); break;
-      case 3: e = launch_patch<T, 3>(h, r, sys0, nsys, fwd, bwd, Xg); break;
-      default: e = launch_patch<T, 4>(h, r, sys0, nsys, fwd, bwd, Xg); break;
+    if constexpr (sizeof(T) == 4) {
+      e = use_tc ? patch_tc_solve(h, Q, r, sys0, nsys, Xg) : patch_tri_solve_f32(h, G, r, sys0, nsys, Xg);
+    } else {
+      e = patch_tri_solve_f64(h, G, r, sys0, nsys, Xg);
     }
     if (e != cudaSuccess) return e;
     prof_end(h->prof, PROF_PATCH, pa, s);
@@ -1775,7 +1454,7 @@ cudaError_t precond_apply_f64(mstopo_handle* h, const double* r, double* z, int 
   Precond& pc = h->pc;
   if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS && part != 1)
     return sgs_apply_f64(h, r, z, sys0, nsys, part);
-  return apply_impl<double>(h, r, z, sys0, nsys, part, pc.d_psi64, pc.d_pf64, pc.d_pb64, pc.d_zp64);
+  return apply_impl<double>(h, r, z, sys0, nsys, part, pc.d_psi64, pc.d_zp64);
 }
 
 cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sys0, int nsys,
@@ -1783,5 +1462,5 @@ cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sy
   Precond& pc = h->pc;
   if (pc.kind == MSTOPO_PREC_MULTIPLICATIVE_SGS && part != 1)
     return sgs_apply_f32(h, r, z, sys0, nsys, part);
-  return apply_impl<float>(h, r, z, sys0, nsys, part, pc.d_psi32, pc.d_pf32, pc.d_pb32, pc.d_zp32);
+  return apply_impl<float>(h, r, z, sys0, nsys, part, pc.d_psi32, pc.d_zp32);
 }
