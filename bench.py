@@ -359,7 +359,10 @@ def run_ours(args, rank: int, world: int):
         free = torch.from_numpy(~np.asarray(big.fixed, dtype=bool).reshape(-1)).to(dev)
         u32 = torch.randn(ns, 2 * nb_nodes, device=dev, dtype=torch.float32) * free
         y32 = torch.empty_like(u32)
-        byts = nb_nodes * 8 * 2 + big.nelx * big.nely * 4 + nb_nodes   # one system
+        # per system u 8 + y 8 B per node (float2) and E 4 B per element; the output mask
+        # (1 B per node) is shared by the systems of one launch and counted once
+        byts = nb_nodes * 8 * 2 + big.nelx * big.nely * 4                # one system
+        mask_b = nb_nodes
 
         def timed(realisation, masked, reps=20):
             for _ in range(5):
@@ -374,14 +377,14 @@ def run_ours(args, rank: int, world: int):
 
         t_all = timed(-1, True)
         t_one = timed(0, False)
-        gbs = ns * byts / (t_all * 1e-3) / 1e9
-        gbs1 = byts / (t_one * 1e-3) / 1e9
+        gbs = (ns * byts + mask_b) / (t_all * 1e-3) / 1e9
+        gbs1 = (byts + 2 * mask_b) / (t_one * 1e-3) / 1e9   # reads the input and output masks
         mv = {"mesh": f"{big.nelx}x{big.nely}", "dofs": 2 * nb_nodes, "systems_per_launch": ns,
               "launch": "flexible-CG configuration (3 realisations, inputs zero at Dirichlet DOFs)",
-              "avg_launch_ms": t_all, "algorithmic_bytes": ns * byts, "gbs": gbs,
+              "avg_launch_ms": t_all, "algorithmic_bytes": ns * byts + mask_b, "gbs": gbs,
               "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
-              "bytes_per_node": "u 8 + y 8 (float2) + E 4/element + mask 1, per system",
-              "single_vector_masked_input": {"avg_launch_ms": t_one, "algorithmic_bytes": byts,
+              "bytes_per_node": "u 8 + y 8 (float2) + E 4/element per system, output mask 1 once per launch",
+              "single_vector_masked_input": {"avg_launch_ms": t_one, "algorithmic_bytes": byts + 2 * mask_b,
                                              "gbs": gbs1, "frac": gbs1 / peaks["hbm_gbs"]}}
         pb.close()
         del u32, y32
@@ -581,12 +584,14 @@ def run_workload(args):
     f = torch.from_numpy(np.ascontiguousarray(wl.force)).cuda()
     rho = torch.from_numpy(np.ascontiguousarray(wl.rho)).cuda()
     out.update({"mesh": [wl.nelx, wl.nely], "dofs": 2 * (wl.nelx + 1) * (wl.nely + 1),
-                "realisations": len(wl.etas), "preconditioner": args.preconditioner})
+                "realisations": len(wl.etas), "preconditioner": args.preconditioner,
+                "patch_kernel": args.patch_kernel})
     precisions = ["mixed"] if args.workload_mixed_only else ["mixed", "fp64"]
     for prec in precisions:
         prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
                          penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=1e-8,
-                         preconditioner=args.preconditioner, max_iter=5000)
+                         preconditioner=args.preconditioner, max_iter=5000,
+                         patch_kernel=args.patch_kernel)
         torch.cuda.synchronize()
         t0 = time.time()
         prob.set_design(rho, wl.rmin, wl.beta, wl.etas, wl.cell)
@@ -621,6 +626,7 @@ def run_workload(args):
 def run_only(args):
     """One kernel in a short loop: 'patch' = FP32 patch solves of a workload's preconditioner
     (apply_precond, MIXED, patches only, realisation 0; default the 1024x512 workload);
+    'solve' = whole MIXED solves of a workload (default the 1024x512 workload);
     'matvec' = FP32 matvec as the flexible CG launches it (all realisations, default the
     3200x4096 mesh, 26.2M DOFs x 3).  --only-workload and
     --only-scale pick another workload or a reduced copy of it."""
@@ -628,7 +634,7 @@ def run_only(args):
     import paper_1411_3923_gb300 as m
     import workloads
     dev = torch.device("cuda", 0)
-    name = args.only_workload or (WORKLOAD if args.only == "patch" else "mbb_c5")
+    name = args.only_workload or (WORKLOAD if args.only in ("patch", "solve") else "mbb_c5")
     wl = workloads.make(name, args.only_scale)
     prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
                      penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision="mixed")
@@ -638,6 +644,11 @@ def run_only(args):
         r = torch.randn((wl.nely + 1, wl.nelx + 1, 2), dtype=torch.float64, device=dev)
         for _ in range(args.reps):
             prob.apply_precond(r, m.MIXED, 2)
+    elif args.only == "solve":   # whole MIXED solves of the workload (after one build)
+        prob.build_preconditioner(-1)
+        f = torch.from_numpy(wl.force).to(dev)
+        for _ in range(args.reps):
+            prob.solve(f, -1)
     else:   # the flexible CG's launch: every realisation, inputs zero at Dirichlet DOFs
         import numpy as np
         free = torch.from_numpy(~np.asarray(wl.fixed, dtype=bool).reshape(-1)).to(dev)
@@ -660,7 +671,7 @@ def main():
                     help="PCG iterations per timed step of the reference arm")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-big-matvec", action="store_true")
-    ap.add_argument("--only", choices=["patch", "matvec"], default=None,
+    ap.add_argument("--only", choices=["patch", "matvec", "solve"], default=None,
                     help="run one kernel in a short loop (for ncu captures) and exit")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--only-workload", default=None)
@@ -673,6 +684,8 @@ def main():
                     help="run the whole path on a named workload (mbb_c1, mbb_c2, mbb_c3, mbb_c5, "
                          "cantilever_batch) and print one JSON line (no benchmark)")
     ap.add_argument("--workload-mixed-only", action="store_true")
+    ap.add_argument("--patch-kernel", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
+                    help="with --workload-run: the FP32 patch-solve kernel")
     ap.add_argument("--preconditioner", default="additive", choices=["additive", "sgs"],
                     help="with --workload-run: the additive two-level Schwarz preconditioner, or "
                          "the paper's multiplicative one (SGS, coarse correction, SGS)")

@@ -286,6 +286,9 @@ typedef struct {
   int64_t builds;              /* preconditioner builds of this handle (explicit + automatic) */
   int32_t base_iterations;     /* iterations of the first solve after the last build, or -1  */
   int32_t rebuild_pending;     /* 1: the next all-realisation solve rebuilds first            */
+  int64_t device_loop_solves;  /* solves of this handle whose iteration loop ran as one CUDA
+                                  graph with device-side convergence tests (the others ran
+                                  host-driven chunks: graphs off or per-kernel profiling on) */
 } mstopo_stats;
 
 /* Turn per-kernel event timing on (1) or off (0) for this handle; resets its counters.

@@ -167,6 +167,7 @@ void mstopo_destroy(mstopo_handle* h) {
   solver_free(h->sv);
   prof_free(h->prof);
   if (h->fcg_graph.exec) cudaGraphExecDestroy(h->fcg_graph.exec);
+  if (h->fcg_graph.loop) cudaGraphExecDestroy(h->fcg_graph.loop);
   void* ptrs[] = {h->d_K0, h->d_nmask, h->d_rho, h->d_rho_tilde, h->d_wsum, h->d_rbar, h->d_drbar,
                   h->d_E64, h->d_E32, h->d_gfine, h->d_gdesign, h->d_w, h->d_flag, h->d_u_all,
                   h->d_f_all, h->d_host_stage};
@@ -485,6 +486,7 @@ mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out) {
   out->builds = h->builds;
   out->base_iterations = h->base_iters;
   out->rebuild_pending = h->rebuild_pending;
+  out->device_loop_solves = h->device_loop_solves;
   for (int k = 0; k < 4; ++k) {
     out->kernel_launches[k] = h->prof.n[k];
     out->kernel_ms[k] = h->prof.ms[k];

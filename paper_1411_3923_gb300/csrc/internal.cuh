@@ -105,6 +105,9 @@ struct FcgScalars {            // per system, on the device
   int status;                  // mstopo_status
   int iters;
   int restart;                 // 1: the next direction is p = z (first step)
+  double rr_last;              // ||r||^2 at the last true-residual recomputation
+  int done;                    // 1: converged or stopped (device-side loop)
+  int repl;                    // true-residual recomputations
 };
 
 struct FcgGraph {              // one captured chunk of flexible-CG iterations
@@ -112,6 +115,12 @@ struct FcgGraph {              // one captured chunk of flexible-CG iterations
   int sys0 = -1, nsys = 0;
   long long generation = -1;
   long long launches = 0;
+  // the whole iteration loop as one graph (conditional nodes: while not converged, if a true
+  // residual is due); launches per loop pass and per true-residual pass
+  cudaGraphExec_t loop = nullptr;
+  int loop_sys0 = -1, loop_nsys = 0;
+  long long loop_generation = -1;
+  long long loop_launches = 0, true_launches = 0;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -198,6 +207,7 @@ struct Solver {
   double* partials = nullptr;       // [MAX_SYS][4][RED_BLOCKS]
   FcgScalars* sc = nullptr;         // [MAX_SYS]
   FcgScalars* h_sc = nullptr;       // pinned host mirror
+  int* loopstat = nullptr;          // [2] device-side loop passes, true-residual passes
 };
 
 struct mstopo_handle {
@@ -234,6 +244,8 @@ struct mstopo_handle {
   cudaStream_t s_side = nullptr;      // side stream of the preconditioner's coarse chain
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs_enabled = 1;
+  int loop_graph_failed = 0;          // the device-side solve loop could not be built: host loop
+  long long device_loop_solves = 0;   // solves that ran the device-side loop
   int patch_tc = -1;                  // FP32 patch solves on the tensor cores: -1 by problem size, 0 off, 1 on
   int inject = 0;                     // test injection (mstopo_inject), consumed by its target
   long long builds = 0;               // preconditioner builds (explicit and automatic)

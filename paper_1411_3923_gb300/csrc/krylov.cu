@@ -15,6 +15,13 @@
 //          true residual f - K x is recomputed in FP64 whenever the recursive one has
 //          dropped by 1e-2 since the last recomputation, and always before declaring
 //          convergence ("reliable updates").
+// Iteration loop: with CUDA graphs on, the whole loop is one graph launch -- a WHILE
+// conditional node around one iteration and a check kernel, an IF node around the FP64
+// true-residual recomputation the check asks for; the check and a continue kernel set the
+// two conditions on the device (converged systems, the iteration cap, a bounded device wait
+// that gave up), so no host round trip happens inside a solve.  Without graphs (and while
+// per-kernel profiling is on) the host takes the same decisions after every iteration, so
+// both loops give the same iterates bit for bit.
 // Every reduction is two-stage (fixed per-CTA partials, then one CTA in fixed order), so
 // results are bitwise repeatable run to run.
 #include <cmath>
@@ -24,7 +31,7 @@
 
 #define RB MSTOPO_RED_BLOCKS
 #define RT 256
-#define FCG_CHUNK 8   // iterations between host checks (one CUDA graph)
+#define FCG_CHUNK 8   // iterations per replayed graph when conditional nodes are unavailable
 
 // --------------------------------------------------------------------------- reductions
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -271,6 +278,60 @@ __global__ void __launch_bounds__(RT) k_residual(const double* __restrict__ f,
   if (threadIdx.x == 0) partials[blockIdx.y * RB + blockIdx.x] = s;
 }
 
+// ----------------------------------------------------------------- device-side loop control
+// After an iteration: the decisions the host loop takes between chunks.  A system whose
+// recursive residual passed the tolerance (k_scalar_rr made it inactive) or, in MIXED, dropped
+// by 1e-4 (squared) since the last recomputation needs the FP64 true residual; a system at the
+// iteration cap stops with MAX_ITER; a failed system stops.  The IF condition is set when any
+// system needs the true residual.
+__global__ void k_fcg_check(FcgScalars* sc, int nsys, int mixed, int max_iter,
+                            cudaGraphConditionalHandle if_true, int* loopstat) {
+  if (threadIdx.x != 0) return;
+  int need = 0;
+  for (int s = 0; s < nsys; ++s) {
+    FcgScalars& c = sc[s];
+    if (c.done) continue;
+    if (c.status != MSTOPO_OK) { c.done = 1; c.active = 0; continue; }
+    if (!c.active) need = 1;
+    else if (mixed && c.rr < 1e-4 * c.rr_last) need = 1;
+    if (c.iters >= max_iter) { c.status = MSTOPO_MAX_ITER; c.done = 1; c.active = 0; }
+  }
+  loopstat[0] += 1;
+  cudaGraphSetConditional(if_true, need ? 1u : 0u);
+}
+
+// After a true-residual recomputation (rr_true[s] = ||f - K x||^2): it replaces the recursive
+// residual of every system; a system within the tolerance is done, the others continue.
+__global__ void k_fcg_after_true(FcgScalars* sc, const double* __restrict__ rr_true, int nsys,
+                                 double tol2, int* loopstat) {
+  if (threadIdx.x != 0) return;
+  for (int s = 0; s < nsys; ++s) {
+    FcgScalars& c = sc[s];
+    c.repl += 1;
+    c.rr = rr_true[s];
+    c.rr_last = rr_true[s];
+    if (c.done) { c.active = 0; continue; }
+    if (rr_true[s] <= tol2 * c.ff) { c.active = 0; c.done = 1; }
+    else c.active = 1;
+  }
+  loopstat[1] += 1;
+}
+
+// WHILE condition: some system still iterating and no bounded device wait gave up (which
+// stops every system with that status).
+__global__ void k_fcg_continue(FcgScalars* sc, int nsys, const int* __restrict__ werr,
+                               cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0) return;
+  const int e = *werr;
+  int more = 0;
+  for (int s = 0; s < nsys; ++s) {
+    FcgScalars& c = sc[s];
+    if (e && !c.done) { c.status = e; c.done = 1; c.active = 0; }
+    if (!c.done) more = 1;
+  }
+  cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
 // --------------------------------------------------------------------------- host driver
 #define CK(x)                                                                   \
   do {                                                                          \
@@ -303,6 +364,7 @@ mstopo_status solver_alloc(mstopo_handle* h) {
   CK(cudaMalloc(&sv.partials, (size_t)MSTOPO_MAX_SYS * 4 * RB * 8));
   CK(cudaMalloc(&sv.sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
   CK(cudaMallocHost(&sv.h_sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
+  CK(cudaMalloc(&sv.loopstat, 2 * sizeof(int)));
   return MSTOPO_OK;
 }
 
@@ -310,7 +372,7 @@ void solver_free(Solver& sv) {
   cudaFree(sv.x); cudaFree(sv.r); cudaFree(sv.f); cudaFree(sv.tmp);
   cudaFree(sv.p64); cudaFree(sv.q64); cudaFree(sv.z64);
   cudaFree(sv.p32); cudaFree(sv.q32); cudaFree(sv.z32); cudaFree(sv.r32);
-  cudaFree(sv.partials); cudaFree(sv.sc);
+  cudaFree(sv.partials); cudaFree(sv.sc); cudaFree(sv.loopstat);
   if (sv.h_sc) cudaFreeHost(sv.h_sc);
   sv = Solver();
 }
@@ -431,10 +493,129 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
     CK(cudaGetLastError());
     return MSTOPO_OK;
   };
-  const int chunk = FCG_CHUNK;
+  // ---- the whole loop as one graph (no host round trip inside the solve) ----
+  bool looped = false;
+  if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed) {
+    FcgGraph& gr = h->fcg_graph;
+    auto build_loop = [&]() -> cudaError_t {
+      cudaGraph_t top = nullptr;
+      cudaError_t e = cudaGraphCreate(&top, 0);
+      if (e != cudaSuccess) return e;
+      struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{top};
+      cudaGraphConditionalHandle wh, ih;
+      if ((e = cudaGraphConditionalHandleCreate(&wh, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+      if ((e = cudaGraphConditionalHandleCreate(&ih, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+      // (the params struct holds a union without a default constructor: zeroed storage)
+      alignas(cudaGraphNodeParams) unsigned char wbuf[sizeof(cudaGraphNodeParams)] = {};
+      cudaGraphNodeParams& wp = *reinterpret_cast<cudaGraphNodeParams*>(wbuf);
+      wp.type = cudaGraphNodeTypeConditional;
+      wp.conditional.handle = wh;
+      wp.conditional.type = cudaGraphCondTypeWhile;
+      wp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      if ((e = cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp)) != cudaSuccess) return e;
+      cudaGraph_t body = wp.conditional.phGraph_out[0];
+      const long long l0 = g_launch_count.load();
+      // loop body: one iteration, the check, the IF node, the continue kernel
+      if ((e = cudaStreamBeginCaptureToGraph(h->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+      mstopo_status cs = iteration();
+      note_launch(), k_fcg_check<<<1, 32, 0, h->s>>>(sv.sc, nsys, mixed ? 1 : 0, h->p.max_iter, ih, sv.loopstat);
+      cudaError_t ce = cudaGetLastError();
+      cudaGraphNode_t inode = nullptr;
+      alignas(cudaGraphNodeParams) unsigned char ibuf[sizeof(cudaGraphNodeParams)] = {};
+      cudaGraphNodeParams& ip = *reinterpret_cast<cudaGraphNodeParams*>(ibuf);
+      if (cs == MSTOPO_OK && ce == cudaSuccess) {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cgraph;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        ce = cudaStreamGetCaptureInfo(h->s, &cst, nullptr, &cgraph, &deps, nullptr, &nd);
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = ih;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        if (ce == cudaSuccess) ce = cudaGraphAddNode(&inode, cgraph, deps, nullptr, nd, &ip);
+        if (ce == cudaSuccess)
+          ce = cudaStreamUpdateCaptureDependencies(h->s, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+      }
+      if (ce == cudaSuccess) {
+        note_launch(), k_fcg_continue<<<1, 32, 0, h->s>>>(sv.sc, nsys, h->d_flag + 1, wh);
+        ce = cudaGetLastError();
+      }
+      cudaGraph_t captured = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(h->s, &captured);
+      if (cs != MSTOPO_OK) return cudaErrorUnknown;
+      if (ce != cudaSuccess) return ce;
+      if (ee != cudaSuccess) return ee;
+      const long long l1 = g_launch_count.load();
+      // IF body: the FP64 true residual of every system and its bookkeeping
+      if ((e = cudaStreamBeginCaptureToGraph(h->s, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+      cs = true_residual(h, sys0, nsys, vtmp);
+      if (cs == MSTOPO_OK) {
+        note_launch(), k_fcg_after_true<<<1, 32, 0, h->s>>>(sv.sc, vtmp, nsys, tol2, sv.loopstat);
+        ce = cudaGetLastError();
+      }
+      ee = cudaStreamEndCapture(h->s, &captured);
+      if (cs != MSTOPO_OK) return cudaErrorUnknown;
+      if (ce != cudaSuccess) return ce;
+      if (ee != cudaSuccess) return ee;
+      const long long l2 = g_launch_count.load();
+      g_launch_count.fetch_sub(l2 - l0);   // counted per executed pass below
+      if ((e = cudaGraphInstantiate(&gr.loop, top, 0)) != cudaSuccess) { gr.loop = nullptr; return e; }
+      gr.loop_launches = l1 - l0;
+      gr.true_launches = l2 - l1;
+      gr.loop_sys0 = sys0;
+      gr.loop_nsys = nsys;
+      gr.loop_generation = h->pc_generation;
+      return cudaSuccess;
+    };
+    if (!gr.loop || gr.loop_sys0 != sys0 || gr.loop_nsys != nsys || gr.loop_generation != h->pc_generation) {
+      if (gr.loop) { cudaGraphExecDestroy(gr.loop); gr.loop = nullptr; }
+      if (build_loop() != cudaSuccess) {
+        // conditional graph nodes unavailable: the host-driven loop below takes over
+        cudaGetLastError();
+        h->loop_graph_failed = 1;
+      }
+    }
+  }
+  int n_open = 0;
+  for (int s = 0; s < nsys; ++s) n_open += !done[s];
+  if (n_open == 0) {
+    looped = true;   // every system already within the tolerance: no iteration at all
+  } else if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed && h->fcg_graph.loop) {
+    FcgGraph& gr = h->fcg_graph;
+    looped = true;
+    h->device_loop_solves++;
+    for (int s = 0; s < nsys; ++s) {
+      sv.h_sc[s].rr_last = rr_last[s];
+      sv.h_sc[s].done = done[s];
+      sv.h_sc[s].repl = 0;
+    }
+    CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemsetAsync(sv.loopstat, 0, 2 * sizeof(int), h->s));
+    CK(cudaGraphLaunch(gr.loop, h->s));
+    int ls[2] = {0, 0}, werr = 0;
+    CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(ls, sv.loopstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(&werr, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    g_launch_count.fetch_add((long long)ls[0] * gr.loop_launches + (long long)ls[1] * gr.true_launches);
+    for (int s = 0; s < nsys; ++s) {
+      done[s] = 1;
+      repl[s] = sv.h_sc[s].repl;
+      if (werr && sv.h_sc[s].status == MSTOPO_OK && sv.h_sc[s].active) sv.h_sc[s].status = werr;
+    }
+  }
+  // Without graphs (or with per-kernel profiling) the host decides after every iteration,
+  // exactly as the device-side loop does, so both take the same path bit for bit.  Only the
+  // fallback for a missing conditional-node runtime replays chunks of iterations.
+  const int chunk = (h->graphs_enabled && !h->prof.on) ? FCG_CHUNK : 1;
   int total_iters = 0;
   bool first_chunk = true;
-  while (true) {
+  while (!looped) {
     int n_active = 0;
     for (int s = 0; s < nsys; ++s) n_active += !done[s];
     if (n_active == 0) break;

@@ -21,8 +21,8 @@
 //   the last, partial block (nb % 32 rows) holds its rows complete, width and stride
 //   32 ceil(nb/32) (+ 2).  A stride of 2 mod 32 words puts the rows a warp reads along a row
 //   on distinct banks; reads along a column take 32 consecutive words.  Entries beyond nb are
-//   zero.  Then B_k as [nb][6] (the 6 columns 2a-2 .. 2a+3 of row 2a+c, zero outside the
-//   line; zero for k = 0).
+//   zero.  Then B_k as [6][nb] (entry q of row 2a+c is column 2a-2+q, zero outside the line;
+//   zero for k = 0): consecutive rows on consecutive banks.
 //
 // Product y = S_k^-1 t: each warp owns 16 rows of a full row block I (lane = row, two lanes
 // per row splitting the reduction) and forms them completely: the chunks (I, J <= I) along
@@ -39,7 +39,6 @@
 namespace {
 
 constexpr int TMAXW = 9;              // warps per CTA: 2 per full row block (nb = 130: 8) + the edge warp
-constexpr int TPF = 4;                // (row, 16-byte chunk) pairs per thread in the vector phases
 
 // bounded wait for a copy this CTA issued (the drain on exit ignores other aborts)
 __device__ __forceinline__ bool tri_wait(uint64_t* bar, uint32_t parity) {
@@ -101,7 +100,7 @@ __device__ __forceinline__ int tri_rowoff(const TriGeom& g, int r) {
 }
 
 // Pack per (system, line): S_k^-1 = Linv_k^T Linv_k (FP64 sums) in the row-block layout, then
-// B_k = A_{k,k-1} as [nb][6].  Linv: [sys][NL][nb][nb] FP64 (lower triangular); B:
+// B_k = A_{k,k-1} as [6][nb].  Linv: [sys][NL][nb][nb] FP64 (lower triangular); B:
 // [sys][NL-1][nb][nb] FP64.  out64 / out32 may be null.
 __global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* __restrict__ B,
                                  int NL, TriGeom g, double* __restrict__ out64,
@@ -125,7 +124,7 @@ __global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* 
         for (int l = r > c ? r : c; l < nb; ++l) v = fma(Lk[(long long)l * nb + r], Lk[(long long)l * nb + c], v);
       }
     } else if (t < g.TB + 6 * nb) {
-      const int u = t - g.TB, r = u / 6, q = u % 6;
+      const int u = t - g.TB, q = u / nb, r = u % nb;
       const int c = 2 * (r >> 1) - 2 + q;
       if (Bk && c >= 0 && c < nb) v = Bk[(long long)r * nb + c];
     }
@@ -137,8 +136,9 @@ __global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* 
 // Groups g0 + blockIdx.x (see PatchGroups): R columns = up to R patches of one type and
 // realisation; right-hand sides gathered from system grp_sys[g] - sys0 of r.  Work buffer
 // Xg: [group][NL][nb][R] holds w_k after the forward sweep, then [group][NL][R][nb] holds x_k.
-// Launched with 32 (2 nfull + (rem > 0)) threads.
-template <typename T, int R, int NBUF, int MINB>
+// Launched with 32 (2 nfull + (rem > 0)) threads; TPF (row, 16-byte chunk) pairs per thread
+// cover the vector phases (nb R / (16 / sizeof(T)) <= TPF x threads).
+template <typename T, int R, int NBUF, int MINB, int TPF>
 __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
     const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
     int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
           for (int qq = 0; qq < 6; ++qq) {
             const int c = cb + qq;
             if (c < 0 || c >= nb) continue;
-            const T bq = Bq[row * 6 + qq];
+            const T bq = Bq[qq * nb + row];
 #pragma unroll
             for (int e = 0; e < VW; ++e) v[e] = fma(-bq, vp[c * R + ch * VW + e], v[e]);
           }
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
             for (int cr = 0; cr < 2; ++cr) {
               const int row = 2 * an + cr;
               const int qq = c - (2 * an - 2);
-              const T bq = Bq[row * 6 + qq];
+              const T bq = Bq[qq * nb + row];
 #pragma unroll
               for (int e = 0; e < VW; ++e) v[e] = fma(bq, vw[row * R + ch * VW + e], v[e]);
             }
@@ -504,10 +504,10 @@ size_t patch_tri_smem(int nb, int R, int nbuf, size_t elem) {
 long long patch_tri_line_elems(int nb) { return tri_geometry(nb).LB; }
 
 // the kernel's thread layout covers this line size: at most 9 warps, rows addressed through
-// a 160-entry table, every vector phase within TPF pairs per thread (16 patches per CTA)
+// a 160-entry table, every vector phase within 4 pairs per thread (16 patches per CTA)
 bool patch_tri_assignment_ok(int nb) {
   const int nt = tri_threads(nb);
-  return nb >= 2 && nb <= 160 && nt <= 32 * TMAXW && nb * 4 <= TPF * nt;
+  return nb >= 2 && nb <= 160 && nt <= 32 * TMAXW && nb * 4 <= 4 * nt;
 }
 
 cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
@@ -517,24 +517,34 @@ cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb
   return cudaGetLastError();
 }
 
-template <typename T, int R, int NBUF>
-static cudaError_t launch_tri_k(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
-                                int nsys, const T* pack, T* Xg) {
+template <typename T, int R, int NBUF, int TPF>
+static cudaError_t launch_tri_kt(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
+                                 int nsys, const T* pack, T* Xg) {
   constexpr int MINB = (sizeof(T) == 4 && R <= 4) ? 2 : 1;   // two CTAs per SM at four columns
   Precond& pc = h->pc;
   const TriGeom geo = tri_geometry(pc.nbP);
   const size_t sm = patch_tri_smem(pc.nbP, R, NBUF, sizeof(T));
   {
-    cudaError_t e = smem_limit_max<k_patch_tri<T, R, NBUF, MINB>>();
+    cudaError_t e = smem_limit_max<k_patch_tri<T, R, NBUF, MINB, TPF>>();
     if (e != cudaSuccess) return e;
   }
   if (sm > 225 * 1024 || !patch_tri_assignment_ok(pc.nbP)) return cudaErrorInvalidConfiguration;
   const int g0 = G.h_begin[sys0], ng = G.h_begin[sys0 + nsys] - g0;
   if (ng <= 0) return cudaSuccess;
-  note_launch(), k_patch_tri<T, R, NBUF, MINB><<<ng, tri_threads(pc.nbP), sm, h->s>>>(
+  note_launch(), k_patch_tri<T, R, NBUF, MINB, TPF><<<ng, tri_threads(pc.nbP), sm, h->s>>>(
       r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, G.d_type, G.d_sys, G.d_first,
       G.d_count, G.d_perm, pc.d_pfree, pack, geo, Xg, h->d_flag + 1);
   return cudaGetLastError();
+}
+
+// one (row, 16-byte chunk) pair per thread when the threads cover the vector phases, else four
+template <typename T, int R, int NBUF>
+static cudaError_t launch_tri_k(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
+                                int nsys, const T* pack, T* Xg) {
+  const int nb = h->pc.nbP;
+  if (nb * (R * (int)sizeof(T) / 16) <= tri_threads(nb))
+    return launch_tri_kt<T, R, NBUF, 1>(h, G, r, sys0, nsys, pack, Xg);
+  return launch_tri_kt<T, R, NBUF, 4>(h, G, r, sys0, nsys, pack, Xg);
 }
 
 cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,

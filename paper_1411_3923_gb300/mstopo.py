@@ -50,7 +50,8 @@ class _BuildInfo(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("kernel_launches", C.c_int64 * 4),
                 ("kernel_ms", C.c_double * 4), ("builds", C.c_int64),
-                ("base_iterations", C.c_int32), ("rebuild_pending", C.c_int32)]
+                ("base_iterations", C.c_int32), ("rebuild_pending", C.c_int32),
+                ("device_loop_solves", C.c_int64)]
 
 
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
@@ -289,7 +290,7 @@ class Problem:
 
 def _stats_dict(st: "_Stats") -> dict:
     out = {"launches": st.launches, "builds": st.builds, "base_iterations": st.base_iterations,
-           "rebuild_pending": st.rebuild_pending}
+           "rebuild_pending": st.rebuild_pending, "device_loop_solves": st.device_loop_solves}
     for name, k in KERNEL_IDS.items():
         out[name] = {"launches": st.kernel_launches[k], "ms": st.kernel_ms[k]}
     return out

@@ -591,3 +591,27 @@ def test_solve_with_multiplicative_sgs(precision, etas):
         ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
         assert_energy(Kf, ur, ug)
         assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-10)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_side_loop_equals_host_driven_loop(precision):
+    """With CUDA graphs the whole flexible-CG loop is one graph launch (a WHILE conditional
+    node, an IF node for the FP64 residual replacement, convergence decided on the device);
+    without graphs the host drives chunks of iterations.  Same kernels, same decisions: the
+    solutions are bitwise equal, three realisations, and the stats show which loop ran."""
+    m = _gpu()
+    wl = workloads.small(96, 48, seed=13, kind="voids", H=8, n_eig=6, etas=(0.3, 0.5, 0.7),
+                         rmin=2.0, beta=8.0)
+    out = {}
+    for graphs in (True, False):
+        prob = make_problem(m, wl, precision, tol=1e-10, graphs=graphs)
+        prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+        prob.build_preconditioner()
+        u, infos = prob.solve(cuda(wl.force), -1)
+        u2, infos2 = prob.solve(cuda(wl.force), -1)
+        assert torch.equal(u, u2)
+        out[graphs] = (u, [i["iterations"] for i in infos], [i["rel_residual"] for i in infos])
+        assert prob.stats()["device_loop_solves"] == (2 if graphs else 0)
+        assert all(i["status"] == 0 and i["rel_residual"] <= 1e-10 for i in infos)
+    assert torch.equal(out[True][0], out[False][0])
+    assert out[True][1] == out[False][1] and out[True][2] == out[False][2]
