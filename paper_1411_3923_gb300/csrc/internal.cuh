@@ -154,22 +154,11 @@ struct Precond {
   // per-system patch matrices: block tridiagonal by node rows of the (2H+1)^2 agglomerate
   // box, artificial-boundary nodes Dirichlet
   uint8_t* d_pfree = nullptr;       // [T][NP*nbP] free DOFs of the patch box
-  // patch solves on the CUDA cores (csrc/patch_tri.cu): per (system, line) the packed
-  // lower-triangular Linv_k and the coupling block B_k, FP64 and FP32 [T*nsv][NL][line]
+  // patch solves on the CUDA cores (csrc/patch_tri.cu): per patch system the packed blocks of
+  // the two-sided elimination (top chain, bottom chain, middle line), FP64 and FP32
+  // [T*nsv][patch_tri_system_elems]
   double* d_tri64 = nullptr;
   float* d_tri32 = nullptr;
-  // patch solves on the CUDA cores from the packed triangular factors (csrc/patch_tri.cu)
-bool patch_tri_assignment_ok(int nb);
-// right-hand-side columns of a CUDA-core patch-solve CTA for groups of up to P patches
-inline int patch_tri_cols(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : 16); }
-long long patch_tri_line_elems(int nb);
-cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
-                           double* out64, float* out32, cudaStream_t s);
-cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
-                                int nsys, float* Xg);
-cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const double* r, int sys0,
-                                int nsys, double* Xg);
-
 // tensor-core FP32 patch solve (csrc/patch_tc.cu): TF32 hi/lo factor lines [T][2][NL][line]
   unsigned char* d_ptc = nullptr;
   long long tc_line_bytes = 0;
@@ -306,13 +295,20 @@ cudaError_t smem_limit_max() {
   return once;
 }
 
-// patch solves on the CUDA cores from the packed triangular factors (csrc/patch_tri.cu)
+// patch solves on the CUDA cores from the two-sided block elimination (csrc/patch_tri.cu)
 bool patch_tri_assignment_ok(int nb);
 // right-hand-side columns of a CUDA-core patch-solve CTA for groups of up to P patches
 inline int patch_tri_cols(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : 16); }
-long long patch_tri_line_elems(int nb);
-cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
-                           double* out64, float* out32, cudaStream_t s);
+// packed elements per patch system (all blocks of both chains and the middle line)
+long long patch_tri_system_elems(int nb, int NL);
+// CTAs of the FP32 kernel that fit on one SM for R columns (shared memory)
+int patch_tri_ctas_per_sm(int nb, int R);
+// Lt: top-down factor [nsys][NL] (Linv_k), Bt: [nsys][NL-1] (A_{k+1,k}); Lr, Br: the same for
+// the first NLr lines of the line-reversed system; Lm: [nsys] inverse factor of the middle
+// line's two-sided Schur complement.  out64 / out32 may be null.
+cudaError_t patch_tri_pack(const double* Lt, const double* Bt, const double* Lr, const double* Br,
+                           const double* Lm, int nsys, int nb, int NL, int NLr, double* out64,
+                           float* out32, cudaStream_t s);
 cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
                                 int nsys, float* Xg);
 cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const double* r, int sys0,

@@ -1,44 +1,69 @@
 // Overlapping patch solves of the additive two-level preconditioner (Sec. 2.4.2: the exact
-// local solves z_i = K_i^-1 R_i r on every agglomerate patch), one CTA per group of patches
-// of one type and realisation (R right-hand sides), streaming one symmetric block per line.
+// local solves z_i = K_i^-1 R_i r on every agglomerate patch) by a two-sided block
+// elimination: one cluster of two CTAs per group of patches of one type and realisation
+// (R right-hand sides), each CTA streaming one symmetric block per line of its half.
 //
-// The patch matrix is block tridiagonal over the NL node rows ("lines") of its box, with
-// diagonal blocks A_k and couplings B_k = A_{k,k-1} (each DOF couples with the 6 DOFs of the
-// three neighbouring nodes of the previous line).  Block elimination gives the Schur
-// complements S_0 = A_0, S_k = A_k - B_k S_{k-1}^-1 B_k^T (S_k = L_k L_k^T in the block
-// Cholesky factor), and with w_k = S_k^-1 (b_k - B_k w_{k-1}) the two sweeps are
-//   forward   w_k = S_k^-1 (b_k - B_k w_{k-1})                       (w_{-1} = 0)
-//   backward  x_k = w_k - S_k^-1 t_k,   t_{k-1} = B_k^T x_k          (t_{NL-1} = 0)
-// i.e. one product with the symmetric S_k^-1 per line and sweep, and two sparse products
-// with B_k.  Per line and right-hand side that is nb^2 multiply-adds on a factor of about
-// nb^2/2 stored entries: the work of a banded triangular solve pair, 4 n b flops per patch
-// and application.  S_k^-1 = L_k^-T L_k^-1 is formed in FP64 and rounded once, so the FP32
-// solve carries one rounding of each factor entry (no product of two inverse factors).
+// The patch matrix is block tridiagonal over the NL = 2H + 1 node rows ("lines") of its box,
+// with diagonal blocks A_k and couplings A_{k,k-1} (each DOF couples with the 6 DOFs of the
+// three neighbouring nodes of the previous line).  The elimination runs from both ends toward
+// the middle line m = H at once ("twisted" order), so the dependent chain is H + 1 lines long
+// instead of NL:
+//   top     S_0 = A_0,        S_k = A_k - A_{k,k-1} S_{k-1}^-1 A_{k-1,k}            k < m
+//   bottom  U_{NL-1} = A_{NL-1}, U_k = A_k - A_{k,k+1} U_{k+1}^-1 A_{k+1,k}         k > m
+//   middle  M = A_m - A_{m,m-1} S_{m-1}^-1 A_{m-1,m} - A_{m,m+1} U_{m+1}^-1 A_{m+1,m}
+// and with the forward sweeps of both halves
+//   w_k = S_k^-1 (b_k - A_{k,k-1} w_{k-1})  (k < m),   v_k = U_k^-1 (b_k - A_{k,k+1} v_{k+1})  (k > m)
+// the solution is
+//   x_m = M^-1 (b_m - A_{m,m-1} w_{m-1} - A_{m,m+1} v_{m+1})
+//   x_k = w_k - S_k^-1 A_{k,k+1} x_{k+1}  (k < m),   x_k = v_k - U_k^-1 A_{k,k-1} x_{k-1}  (k > m).
+// The bottom half is the top half of the line-reversed matrix, so both CTAs run the same
+// "chain": line j of CTA rank 1 is patch line NL-1-j, and its coupling block is A_{l,l+1}.
+// Per line and right-hand side that is one product with a symmetric inverse (nb^2
+// multiply-adds on about nb^2/2 stored entries) and two sparse products with the coupling:
+// the work of a banded triangular solve pair, 4 n b flops per patch and application.  The
+// inverses are formed in FP64 (S^-1 = L^-T L^-1) and rounded once.
 //
-// Packed line block (one cp.async.bulk per line, ring of NBUF stages in shared memory):
-//   rows of S_k^-1 in row blocks of 32: block I < nfull holds 32 rows of width 32(I+1) (the
-//   lower triangle by 32 x 32 chunks, the diagonal chunk complete) at row stride 32(I+1) + 2;
-//   the last, partial block (nb % 32 rows) holds its rows complete, width and stride
-//   32 ceil(nb/32) (+ 2).  A stride of 2 mod 32 words puts the rows a warp reads along a row
-//   on distinct banks; reads along a column take 32 consecutive words.  Entries beyond nb are
-//   zero.  Then B_k as [6][nb] (entry q of row 2a+c is column 2a-2+q, zero outside the line;
-//   zero for k = 0): consecutive rows on consecutive banks.
+// Packed block (one cp.async.bulk each, ring of NBUF stages in shared memory):
+//   rows of the symmetric inverse in row blocks of 32: block I < nfull holds 32 rows of width
+//   32(I+1) (the lower triangle by 32 x 32 chunks, the diagonal chunk complete) at row stride
+//   32(I+1) + 2; the last, partial block (nb % 32 rows) holds its rows complete, width and
+//   stride 32 ceil(nb/32) (+ 2).  A stride of 2 mod 32 words puts the rows a warp reads along
+//   a row on distinct banks; reads along a column take 32 consecutive words.  Entries beyond
+//   nb are zero.  Then the coupling as [6][nb] (entry q of row 2a+c is column 2a-2+q of the
+//   neighbouring line, zero outside it; zero for the first line of a chain).  The middle
+//   block carries two couplings, A_{m,m-1} (rank 0's) then A_{m,m+1} (rank 1's).
+// Per patch system: chain blocks of rank 0 (lines 0..H-1), of rank 1 (lines NL-1..H+1), then
+// the middle block.
 //
-// Product y = S_k^-1 t: each warp owns 16 rows of a full row block I (lane = row, two lanes
+// Product y = S^-1 t: each warp owns 16 rows of a full row block I (lane = row, two lanes
 // per row splitting the reduction) and forms them completely: the chunks (I, J <= I) along
-// the rows (float2 loads, conflict-free at a stride of 2 mod 32 words), the chunks (J' > I, I)
-// below them down their columns, and the rank-rem contribution of the partial block's rows;
-// every row block costs the same nfull chunks, so the warps are balanced and no partial sums
-// cross warps.  One more warp forms the partial block's complete rows (lanes over columns,
-// warp reduction in a fixed order): the result is bitwise repeatable.  Every wait is bounded;
-// on a timeout the CTA records MSTOPO_TIMEOUT, stops, waits (bounded) for the copies it issued
-// and exits.
+// the rows (pairs of columns), the chunks (J' > I, I) below them down their columns (pairs of
+// rows), and the partial block's rows; the partial sums of even and odd columns are carried
+// as pairs (one paired FP32 FMA per matrix pair and right-hand side).  Every row block costs
+// the same nfull chunks, so the warps are balanced and no partial sums cross warps.  One more
+// warp forms the partial block's complete rows (lanes over column pairs, warp reduction in a
+// fixed order).  Vectors are [R][NV] in shared memory; the vector phases map one thread to a
+// (node, right-hand side) pair.  The results are bitwise repeatable.
+//
+// The two CTAs meet once, at the middle line: each publishes its coupling contribution in its
+// own shared memory, both cross a cluster barrier, and both form x_m from the two
+// contributions in the same order (identical bits), so nothing else is exchanged.  Every
+// mbarrier wait is bounded; on a timeout the CTA records MSTOPO_TIMEOUT, stops computing, still
+// crosses both cluster barriers (the partner never waits forever), waits (bounded) for the
+// copies it issued and exits.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "blocktri.cuh"
 #include "internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace {
 
-constexpr int TMAXW = 9;              // warps per CTA: 2 per full row block (nb = 130: 8) + the edge warp
+constexpr int TMAXW = 9;        // warps per CTA: 2 per full row block (nb = 130: 8) + the edge warp
+constexpr int TMINTH = 128;     // at least this many threads (small boxes: the vector phases)
 
 // bounded wait for a copy this CTA issued (the drain on exit ignores other aborts)
 __device__ __forceinline__ bool tri_wait(uint64_t* bar, uint32_t parity) {
@@ -47,35 +72,42 @@ __device__ __forceinline__ bool tri_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// R consecutive T values -> registers (16-byte accesses; R a multiple of 16 / sizeof(T))
-template <typename T, int R>
-__device__ __forceinline__ void ld_row(const T* p, T (&v)[R]) {
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// c + a * b elementwise on a pair: one paired FP32 FMA, two FP64 FMAs
+__device__ __forceinline__ float2 fma_pair(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma_pair(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// four consecutive T as two pairs (16-byte aligned)
+template <typename T, typename V2>
+__device__ __forceinline__ void ld_quad(const T* p, V2& lo, V2& hi) {
   if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int j = 0; j < R; j += 4) {
-      const float4 q = *reinterpret_cast<const float4*>(p + j);
-      v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
-    }
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    lo = make_float2(q.x, q.y);
+    hi = make_float2(q.z, q.w);
   } else {
-#pragma unroll
-    for (int j = 0; j < R; j += 2) {
-      const double2 q = *reinterpret_cast<const double2*>(p + j);
-      v[j] = q.x; v[j + 1] = q.y;
-    }
+    lo = *reinterpret_cast<const double2*>(p);
+    hi = *reinterpret_cast<const double2*>(p + 2);
   }
 }
 
 }  // namespace
 
-// Geometry of one packed line block (host and device).
+// Geometry of one packed block (host and device).
 struct TriGeom {
   int nb, nfull, rem, nrb;   // DOFs per line, full 32-row blocks, rows of the last block, row blocks
   int S[6], off[6];          // row stride and offset of every row block
-  int TB, LB;                // offset of the coupling block; elements per line block (16-byte multiple)
+  int TB;                    // offset of the coupling block(s)
+  int LB, LBM;               // elements of a chain block / of the middle block (16-byte multiples)
   int NV;                    // rows of the shared-memory vectors (32 nrb, zero beyond nb)
+  long long SS;              // elements per patch system
 };
 
-TriGeom tri_geometry(int nb) {
+static TriGeom tri_geometry(int nb, int NL) {
   TriGeom g{};
   g.nb = nb;
   g.nfull = nb / 32;
@@ -89,29 +121,52 @@ TriGeom tri_geometry(int nb) {
     o += (full ? 32 : g.rem) * g.S[I];
   }
   g.TB = (o + 3) / 4 * 4;
-  g.LB = (g.TB + 6 * nb + 3) / 4 * 4;
+  g.LB = g.TB + 6 * nb;    // nb even: 6 nb is a multiple of 4
+  g.LBM = g.TB + 12 * nb;
   g.NV = 32 * g.nrb;
+  g.SS = (long long)(NL - 1) * g.LB + g.LBM;
   return g;
 }
 
+// offset of factor row r in a block, in closed form (no dynamic indexing of the geometry):
+// full row block I starts at sum_{i<I} 32 (32 (i + 1) + 2) = 512 I (I + 1) + 64 I
 __device__ __forceinline__ int tri_rowoff(const TriGeom& g, int r) {
   const int I = r >> 5;
-  return g.off[I] + (r & 31) * g.S[I];
+  const int S = (I < g.nfull ? 32 * (I + 1) : 32 * g.nrb) + 2;
+  return 512 * I * (I + 1) + 64 * I + (r & 31) * S;
 }
 
-// Pack per (system, line): S_k^-1 = Linv_k^T Linv_k (FP64 sums) in the row-block layout, then
-// B_k = A_{k,k-1} as [6][nb].  Linv: [sys][NL][nb][nb] FP64 (lower triangular); B:
-// [sys][NL-1][nb][nb] FP64.  out64 / out32 may be null.
-__global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* __restrict__ B,
-                                 int NL, TriGeom g, double* __restrict__ out64,
-                                 float* __restrict__ out32) {
-  const int sys = blockIdx.x, k = blockIdx.y;
-  const int nb = g.nb;
+// Pack per (system, block b): b < H the top chain (line b: Linv_b of the top-down factor,
+// coupling A_{b,b-1} = Bt[b-1]); H <= b < 2H the bottom chain (reversed line j = b - H: Linv
+// of the reversed factor, coupling A'_{j,j-1} = Br[j-1]); b = 2H the middle line (M^-1 from
+// Lm, couplings A_{m,m-1} = Bt[m-1] and A_{m,m+1} = Br[m-1]).  The symmetric inverse is
+// (Linv^T Linv)[r][c] = sum over l >= max(r, c) of Linv[l][r] Linv[l][c], in FP64.
+__global__ void k_patch_tri_pack(const double* __restrict__ Lt, const double* __restrict__ Bt,
+                                 const double* __restrict__ Lr, const double* __restrict__ Br,
+                                 const double* __restrict__ Lm, int NL, int NLr, TriGeom g,
+                                 double* __restrict__ out64, float* __restrict__ out32) {
+  const int sys = blockIdx.x, b = blockIdx.y;
+  const int nb = g.nb, H = (NL - 1) / 2;
   const long long nn = (long long)nb * nb;
-  const double* Lk = Linv + ((long long)sys * NL + k) * nn;
-  const double* Bk = k > 0 ? B + ((long long)sys * (NL - 1) + k - 1) * nn : nullptr;
-  const long long o = ((long long)sys * NL + k) * g.LB;
-  for (int t = threadIdx.x; t < g.LB; t += blockDim.x) {
+  const double* Li;
+  const double* C0 = nullptr;
+  const double* C1 = nullptr;
+  int size = g.LB;
+  if (b < H) {
+    Li = Lt + ((long long)sys * NL + b) * nn;
+    if (b > 0) C0 = Bt + ((long long)sys * (NL - 1) + b - 1) * nn;
+  } else if (b < 2 * H) {
+    const int j = b - H;
+    Li = Lr + ((long long)sys * NLr + j) * nn;
+    if (j > 0) C0 = Br + ((long long)sys * (NLr - 1) + j - 1) * nn;
+  } else {
+    Li = Lm + (long long)sys * nn;
+    C0 = Bt + ((long long)sys * (NL - 1) + H - 1) * nn;
+    C1 = Br + ((long long)sys * (NLr - 1) + H - 1) * nn;
+    size = g.LBM;
+  }
+  const long long o = (long long)sys * g.SS + (long long)b * g.LB;
+  for (int t = threadIdx.x; t < size; t += blockDim.x) {
     double v = 0.0;
     if (t < g.TB) {
       int I = g.nrb - 1;
@@ -120,12 +175,13 @@ __global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* 
       const int r = 32 * I + u / g.S[I], c = u % g.S[I];
       const int width = I < g.nfull ? 32 * (I + 1) : nb;
       if (r < nb && c < nb && c < width) {
-        // (Linv^T Linv)[r][c] = sum over l >= max(r, c) of Linv[l][r] Linv[l][c]
-        for (int l = r > c ? r : c; l < nb; ++l) v = fma(Lk[(long long)l * nb + r], Lk[(long long)l * nb + c], v);
+        for (int l = r > c ? r : c; l < nb; ++l) v = fma(Li[(long long)l * nb + r], Li[(long long)l * nb + c], v);
       }
-    } else if (t < g.TB + 6 * nb) {
-      const int u = t - g.TB, q = u / nb, r = u % nb;
+    } else {
+      const int u = t - g.TB, rho = u / (6 * nb), u2 = u % (6 * nb);
+      const int q = u2 / nb, r = u2 % nb;
       const int c = 2 * (r >> 1) - 2 + q;
+      const double* Bk = rho == 0 ? C0 : C1;
       if (Bk && c >= 0 && c < nb) v = Bk[(long long)r * nb + c];
     }
     if (out64) out64[o + t] = v;
@@ -133,47 +189,57 @@ __global__ void k_patch_tri_pack(const double* __restrict__ Linv, const double* 
   }
 }
 
-// Groups g0 + blockIdx.x (see PatchGroups): R columns = up to R patches of one type and
+// Groups g0 + blockIdx.x / 2 (see PatchGroups): R columns = up to R patches of one type and
 // realisation; right-hand sides gathered from system grp_sys[g] - sys0 of r.  Work buffer
-// Xg: [group][NL][nb][R] holds w_k after the forward sweep, then [group][NL][R][nb] holds x_k.
-// Launched with 32 (2 nfull + (rem > 0)) threads; TPF (row, 16-byte chunk) pairs per thread
-// cover the vector phases (nb R / (16 / sizeof(T)) <= TPF x threads).
+// Xg: [group][NL][R][nb] holds w_k after the forward sweeps, then x_k.  Launched as clusters
+// of two CTAs (rank 0 the top half, rank 1 the bottom half) of max(32 (2 nfull + (rem > 0)),
+// 128) threads; TPF (node, right-hand side) pairs per thread cover the vector phases
+// (nb / 2 R <= TPF x threads).
 template <typename T, int R, int NBUF, int MINB, int TPF>
-__global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
     const T* __restrict__ r, long long stride, int sys0, int g0, int nelx, int nely, int H,
     int ncx, const int* __restrict__ grp_type, const int* __restrict__ grp_sys,
     const int* __restrict__ grp_first, const int* __restrict__ grp_count,
     const int* __restrict__ perm, const uint8_t* __restrict__ pfree, const T* __restrict__ pack,
     TriGeom geo, T* __restrict__ Xg, int* __restrict__ err) {
-  constexpr int VW = 16 / sizeof(T);          // elements per 16-byte chunk
-  constexpr int RC = R / VW;                  // chunks per vector row
-  static_assert(R % VW == 0, "R must fill 16-byte chunks");
+  using V2 = typename Pair<T>::type;
   __shared__ __align__(8) uint64_t bars[NBUF];
   __shared__ int s_abort;
-  __shared__ int s_node[16];
-  __shared__ int s_rowoff[160];               // offset of every factor row in a line block
+  __shared__ int s_ox[16], s_oy[16];          // lower-left node of each patch's box
+  __shared__ int s_rowoff[160];               // offset of every factor row in a block
   extern __shared__ __align__(16) unsigned char smraw[];
 
-  const int nb = geo.nb, NV = geo.NV, nfull = geo.nfull, rem = geo.rem;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int nb = geo.nb, NV = geo.NV, nfull = geo.nfull, rem = geo.rem, NN = nb >> 1;
   const int nrw = 2 * nfull;                  // row warps (16 rows each); warp nrw is the edge warp
   const int NTH = blockDim.x;
-  const int N = 2 * H + 1, NL = N;
-  const int grp = g0 + blockIdx.x;
+  const int N = 2 * H + 1, NL = N, Lc = H;    // lines of the box; chain length; middle line Lc
+  const int grp = g0 + (blockIdx.x >> 1);
   const int type = grp_type[grp], first = grp_first[grp], cnt = grp_count[grp];
   const T* rs = r + (long long)(grp_sys[grp] - sys0) * stride;
   const uint8_t* fr = pfree + (long long)type * N * nb;
-  const T* src = pack + (long long)type * NL * geo.LB;
+  const T* src = pack + (long long)type * geo.SS;
   T* X = Xg + (long long)grp * NL * R * nb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool edge_warp = warp == nrw;
 
-  T* ring = reinterpret_cast<T*>(smraw);                  // [NBUF][LB]
-  T* vt = ring + (long long)NBUF * geo.LB;                // [NV][R] input t of the product
-  T* vy = vt + NV * R;                                    // [NV][R] its result S^-1 t
-  T* vw = vy + NV * R;                                    // [NV][R] w_k or x_k
-  T* vp = vw + NV * R;                                    // [NV][R] w_{k-1} (forward)
+  T* ring = reinterpret_cast<T*>(smraw);                  // [NBUF][LBM]
+  T* vt = ring + (long long)NBUF * geo.LBM;               // [R][NV] input t of the product
+  T* vy = vt + NV * R;                                    // [R][NV] its result S^-1 t
+  T* vw = vy + NV * R;                                    // [R][NV] x of the current line
+  T* vp = vw + NV * R;                                    // [R][NV] w of the previous line
+  T* vu = vp + NV * R;                                    // [R][NV] this CTA's middle contribution
 
-  if (tid < 16) s_node[tid] = tid < cnt ? perm[first + tid] : -1;
+  if (tid < 16) {
+    int ox = 0, oy = 0;
+    if (tid < cnt) {
+      const int ia = perm[first + tid];
+      ox = (ia % (ncx + 1) - 1) * H;
+      oy = (ia / (ncx + 1) - 1) * H;
+    }
+    s_ox[tid] = ox;
+    s_oy[tid] = oy;
+  }
   for (int q = tid; q < nb; q += NTH) s_rowoff[q] = tri_rowoff(geo, q);
   if (tid == 0) {
     s_abort = 0;
@@ -181,60 +247,120 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero the vectors (rows nb..NV-1 stay zero for the whole solve)
-  for (int q = tid; q < 4 * NV * R; q += NTH) vt[q] = T(0);
+  for (int q = tid; q < 5 * NV * R; q += NTH) vt[q] = T(0);
   __syncthreads();
 
-  // ---- line-block stream: sequence m = 0 .. 2NL-1, line(m) = m (forward), 2NL-1-m (backward)
-  const int nseq = 2 * NL;
-  const uint32_t bytes = (uint32_t)((long long)geo.LB * sizeof(T));
-  auto line_of = [&](int m) { return m < NL ? m : 2 * NL - 1 - m; };
+  // ---- block stream: s = 0 .. 2 Lc; s < Lc forward chain line s, s = Lc the middle line,
+  //      s > Lc backward chain line 2 Lc - s.  Chain line j is patch line j (rank 0) or
+  //      NL - 1 - j (rank 1).
+  const int nseq = 2 * Lc + 1;
+  auto line_of = [&](int j) { return rank ? NL - 1 - j : j; };
+  auto block_off = [&](int s) -> long long {
+    if (s == Lc) return (long long)(NL - 1) * geo.LB;
+    const int j = s < Lc ? s : 2 * Lc - s;
+    return (long long)(rank * Lc + j) * geo.LB;
+  };
+  auto block_bytes = [&](int s) -> uint32_t {
+    return (uint32_t)((long long)(s == Lc ? geo.LBM : geo.LB) * sizeof(T));
+  };
   int issued = 0;   // copies issued (thread 0's count)
   if (tid == 0)
     for (; issued < NBUF && issued < nseq; ++issued) {
-      mbar_expect_tx(&bars[issued], bytes);
-      bulk_g2s(ring + (long long)issued * geo.LB, src + (long long)line_of(issued) * geo.LB, bytes,
+      mbar_expect_tx(&bars[issued], block_bytes(issued));
+      bulk_g2s(ring + (long long)issued * geo.LBM, src + block_off(issued), block_bytes(issued),
                &bars[issued]);
     }
   uint32_t phase = 0u;   // bit b: parity of the next wait on stage b
 
-  // vector phases: (row, 16-byte chunk) pairs q = tid + s NTH, s < TPF (nb RC <= TPF NTH)
-  T pf[TPF][VW];                                   // next line's input chunks
-  auto gather = [&](int k, T (&dst)[TPF][VW]) {    // forward input b_k: r at the patch's DOFs
+  // vector phases: (node a, right-hand side jj) pairs q = tid + s NTH, s < TPF
+  int qa[TPF], qj[TPF];
+  bool qv[TPF];
+#pragma unroll
+  for (int s = 0; s < TPF; ++s) {
+    const int q = tid + s * NTH;
+    qv[s] = q < NN * R;
+    qa[s] = q % NN;
+    qj[s] = q / NN;
+  }
+  V2 pf[TPF];   // the next line's input pairs
+  auto gather = [&](int l, V2 (&dst)[TPF]) {   // b_l: r at the patch's DOFs of line l
 #pragma unroll
     for (int s = 0; s < TPF; ++s) {
-      const int q = tid + s * NTH;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) dst[s][e] = T(0);
-      if (q >= nb * RC) continue;
-      const int row = q / RC, ch = q % RC;
-      if (!fr[(long long)k * nb + row]) continue;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        const int p = ch * VW + e;
-        if (p < cnt) {
-          const int ia = s_node[p];
-          const int I = ia % (ncx + 1), J = ia / (ncx + 1);
-          const int x = (I - 1) * H + (row >> 1), y = (J - 1) * H + k;
-          if (x >= 0 && x <= nelx && y >= 0 && y <= nely)
-            dst[s][e] = rs[2 * ((long long)y * (nelx + 1) + x) + (row & 1)];
+      V2 v;
+      v.x = T(0);
+      v.y = T(0);
+      const int a = qa[s], jj = qj[s];
+      if (qv[s] && jj < cnt) {
+        const int x = s_ox[jj] + a, y = s_oy[jj] + l;
+        if (x >= 0 && x <= nelx && y >= 0 && y <= nely) {
+          const V2 g = *reinterpret_cast<const V2*>(rs + 2 * ((long long)y * (nelx + 1) + x));
+          const uint8_t* f = fr + (long long)l * nb + 2 * a;
+          if (f[0]) v.x = g.x;
+          if (f[1]) v.y = g.y;
         }
       }
+      dst[s] = v;
     }
   };
-  auto load_w = [&](int k, T (&dst)[TPF][VW]) {   // w_k from the work buffer ([nb][R])
+  auto load_w = [&](int l, V2 (&dst)[TPF]) {   // w of patch line l from the work buffer
+#pragma unroll
+    for (int s = 0; s < TPF; ++s)
+      if (qv[s]) dst[s] = *reinterpret_cast<const V2*>(X + ((long long)l * R + qj[s]) * nb + 2 * qa[s]);
+  };
+  auto store_line = [&](int l, const T* v) {   // v ([R][NV]) to the work buffer slot of line l
+#pragma unroll
+    for (int s = 0; s < TPF; ++s)
+      if (qv[s])
+        *reinterpret_cast<V2*>(X + ((long long)l * R + qj[s]) * nb + 2 * qa[s]) =
+            *reinterpret_cast<const V2*>(v + qj[s] * NV + 2 * qa[s]);
+  };
+  // out = base + sign C w: rows of this line, C = [6][nb] coupling, w = the neighbour line
+  // (base: the prefetched input b, or zero)
+  auto couple = [&](const T* C, const T* w, T sign, bool with_base, T* out) {
 #pragma unroll
     for (int s = 0; s < TPF; ++s) {
-      const int q = tid + s * NTH;
-      if (q >= nb * RC) continue;
-      const int row = q / RC, ch = q % RC;
-      const T* p = X + ((long long)k * nb + row) * R + ch * VW;
-      if constexpr (sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        dst[s][0] = v.x; dst[s][1] = v.y; dst[s][2] = v.z; dst[s][3] = v.w;
-      } else {
-        const double2 v = *reinterpret_cast<const double2*>(p);
-        dst[s][0] = v.x; dst[s][1] = v.y;
+      if (!qv[s]) continue;
+      const int a = qa[s], jj = qj[s];
+      V2 t;
+      t.x = with_base ? pf[s].x : T(0);
+      t.y = with_base ? pf[s].y : T(0);
+      const T* wj = w + jj * NV;
+#pragma unroll
+      for (int qq = 0; qq < 6; ++qq) {
+        const int c = 2 * a - 2 + qq;
+        if (c < 0 || c >= nb) continue;
+        const T wv = sign * wj[c];
+        t.x = fma(C[qq * nb + 2 * a], wv, t.x);
+        t.y = fma(C[qq * nb + 2 * a + 1], wv, t.y);
       }
+      *reinterpret_cast<V2*>(out + jj * NV + 2 * a) = t;
+    }
+  };
+  // out = C^T x: column c = 2a + e of the neighbour line gathers the rows of nodes a-1..a+1
+  auto couple_t = [&](const T* C, const T* x, T* out) {
+#pragma unroll
+    for (int s = 0; s < TPF; ++s) {
+      if (!qv[s]) continue;
+      const int a = qa[s], jj = qj[s];
+      const T* xj = x + jj * NV;
+      T t0 = T(0), t1 = T(0);
+#pragma unroll
+      for (int dn = -1; dn <= 1; ++dn) {
+        const int n = a + dn;
+        if (n < 0 || n >= NN) continue;
+        const int q0 = 2 - 2 * dn;               // column 2a is entry q0 of rows 2n, 2n + 1
+        const V2 xv = *reinterpret_cast<const V2*>(xj + 2 * n);
+        const V2 cA = *reinterpret_cast<const V2*>(C + q0 * nb + 2 * n);
+        const V2 cB = *reinterpret_cast<const V2*>(C + (q0 + 1) * nb + 2 * n);
+        t0 = fma(cA.x, xv.x, t0);
+        t0 = fma(cA.y, xv.y, t0);
+        t1 = fma(cB.x, xv.x, t1);
+        t1 = fma(cB.y, xv.y, t1);
+      }
+      V2 t;
+      t.x = t0;
+      t.y = t1;
+      *reinterpret_cast<V2*>(out + jj * NV + 2 * a) = t;
     }
   };
 
@@ -245,115 +371,111 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
       const int I = warp >> 1, i = lane & 15, h = lane >> 4;
       const int row = 16 * warp + i;
       const int col = row - 32 * I;              // the row's column inside chunks (J' > I, I)
-      T acc[R], acc1[R];          // even and odd columns: two independent FMA chains
+      V2 acc[R];                                 // (even, odd) columns of every right-hand side
 #pragma unroll
-      for (int j = 0; j < R; ++j) { acc[j] = T(0); acc1[j] = T(0); }
-      // chunks (I, J <= I) along the row: columns 32 J + 16 h .. + 15, in pairs
+      for (int j = 0; j < R; ++j) {
+        acc[j].x = T(0);
+        acc[j].y = T(0);
+      }
+      // chunks (I, J <= I) along the row: columns 32 J + 16 h .. + 15, by pairs
       const T* Lr = L + s_rowoff[row] + 16 * h;
       for (int J = 0; J <= I; ++J) {
-        const T* Lc = Lr + 32 * J;
-        const T* tv = vt + (long long)(32 * J + 16 * h) * R;
+        const T* Lc_ = Lr + 32 * J;
+        const T* tv = vt + 32 * J + 16 * h;
 #pragma unroll
-        for (int c = 0; c < 16; c += 2) {
-          T a0, a1;
-          if constexpr (sizeof(T) == 4) {
-            const float2 a = *reinterpret_cast<const float2*>(Lc + c);
-            a0 = a.x; a1 = a.y;
-          } else {
-            a0 = Lc[c]; a1 = Lc[c + 1];
+        for (int c = 0; c < 16; c += 4) {
+          const V2 m01 = *reinterpret_cast<const V2*>(Lc_ + c);
+          const V2 m23 = *reinterpret_cast<const V2*>(Lc_ + c + 2);
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            V2 v01, v23;
+            ld_quad<T, V2>(tv + j * NV + c, v01, v23);
+            acc[j] = fma_pair(m01, v01, acc[j]);
+            acc[j] = fma_pair(m23, v23, acc[j]);
           }
-          T v0[R], v1[R];
-          ld_row<T, R>(tv + c * R, v0);
-          ld_row<T, R>(tv + (c + 1) * R, v1);
-#pragma unroll
-          for (int j = 0; j < R; ++j) { acc[j] = fma(a0, v0[j], acc[j]); acc1[j] = fma(a1, v1[j], acc1[j]); }
         }
       }
-#pragma unroll
-      for (int j = 0; j < R; ++j) acc[j] += acc1[j];
       // chunks (J' > I, I) down column `col`: half h takes the rows 32 J' + {0..7, 16..23} + 8 h
-      // (8 rows apart, the two halves read disjoint banks)
+      // (8 rows apart, the two halves read disjoint banks), by pairs of rows
       for (int J2 = I + 1; J2 < nfull; ++J2) {
         const int S2 = 32 * (J2 + 1) + 2;                       // row stride of block J2
         const T* La = L + s_rowoff[32 * J2 + 8 * h] + 32 * I + col;
-        const T* ta = vt + (long long)(32 * J2 + 8 * h) * R;
-        T acc2[R];
+        const T* ta = vt + 32 * J2 + 8 * h;
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc2[j] = T(0);
+        for (int g4 = 0; g4 < 4; ++g4) {
+          const int dr = (g4 & 1) * 4 + (g4 >> 1) * 16;         // 0, 4, 16, 20
+          V2 m01, m23;
+          m01.x = La[dr * S2];
+          m01.y = La[(dr + 1) * S2];
+          m23.x = La[(dr + 2) * S2];
+          m23.y = La[(dr + 3) * S2];
 #pragma unroll
-        for (int s2 = 0; s2 < 16; ++s2) {
-          const int dr = (s2 & 7) + ((s2 >> 3) << 4);           // 0..7, 16..23
-          const T a = La[dr * S2];
-          T v[R];
-          ld_row<T, R>(ta + dr * R, v);
-          if (s2 & 1) {
-#pragma unroll
-            for (int j = 0; j < R; ++j) acc2[j] = fma(a, v[j], acc2[j]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < R; ++j) acc[j] = fma(a, v[j], acc[j]);
+          for (int j = 0; j < R; ++j) {
+            V2 v01, v23;
+            ld_quad<T, V2>(ta + j * NV + dr, v01, v23);
+            acc[j] = fma_pair(m01, v01, acc[j]);
+            acc[j] = fma_pair(m23, v23, acc[j]);
           }
         }
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] += acc2[j];
       }
       // the partial block's rows (complete rows stored): column `row` of each
       for (int e = h; e < rem; e += 2) {
         const int rw = 32 * nfull + e;
         const T a = L[s_rowoff[rw] + row];
-        T v[R];
-        ld_row<T, R>(vt + (long long)rw * R, v);
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] = fma(a, v[j], acc[j]);
+        for (int j = 0; j < R; ++j) acc[j].x = fma(a, vt[j * NV + rw], acc[j].x);
       }
 #pragma unroll
-      for (int j = 0; j < R; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 16);
-      if (h == 0) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) vy[(long long)row * R + j] = acc[j];
+      for (int j = 0; j < R; ++j) {
+        T s = acc[j].x + acc[j].y;
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        if (h == 0) vy[j * NV + row] = s;
       }
-    } else if (edge_warp) {
-      // complete rows of the partial block
+    } else if (warp == nrw && rem > 0) {
+      // complete rows of the partial block: lanes over column pairs
       for (int e0 = 0; e0 < rem; e0 += 2) {
         const int r0 = 32 * nfull + e0, r1 = r0 + 1 < nb ? r0 + 1 : r0;
         const T* L0 = L + s_rowoff[r0];
         const T* L1 = L + s_rowoff[r1];
-        T a0[R], a1[R];
+        V2 a0[R], a1[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) { a0[j] = T(0); a1[j] = T(0); }
-        for (int c = lane; c < NV; c += 32) {
-          T v[R];
-          ld_row<T, R>(vt + (long long)c * R, v);
-          const T l0 = L0[c], l1 = L1[c];
-#pragma unroll
-          for (int j = 0; j < R; ++j) { a0[j] = fma(l0, v[j], a0[j]); a1[j] = fma(l1, v[j], a1[j]); }
+        for (int j = 0; j < R; ++j) {
+          a0[j].x = T(0); a0[j].y = T(0);
+          a1[j].x = T(0); a1[j].y = T(0);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+        for (int c = 2 * lane; c < NV; c += 64) {
+          const V2 l0 = *reinterpret_cast<const V2*>(L0 + c);
+          const V2 l1 = *reinterpret_cast<const V2*>(L1 + c);
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            a0[j] += __shfl_xor_sync(0xffffffffu, a0[j], o);
-            a1[j] += __shfl_xor_sync(0xffffffffu, a1[j], o);
+            const V2 v = *reinterpret_cast<const V2*>(vt + j * NV + c);
+            a0[j] = fma_pair(l0, v, a0[j]);
+            a1[j] = fma_pair(l1, v, a1[j]);
           }
-        if (lane == 0) {
+        }
 #pragma unroll
-          for (int j = 0; j < R; ++j) vy[(long long)r0 * R + j] = a0[j];
-          if (r1 != r0) {
+        for (int j = 0; j < R; ++j) {
+          T s0 = a0[j].x + a0[j].y, s1 = a1[j].x + a1[j].y;
 #pragma unroll
-            for (int j = 0; j < R; ++j) vy[(long long)r1 * R + j] = a1[j];
+          for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          }
+          if (lane == 0) {
+            vy[j * NV + r0] = s0;
+            if (r1 != r0) vy[j * NV + r1] = s1;
           }
         }
       }
     }
   };
-  auto result = [&](int q) -> T { return vy[q]; };
 
-  T wk[TPF][VW];                 // backward: w_k of the current line (registers)
-  gather(0, pf);
-  bool abort = false;
-  // thread 0 waits for the block of step m before a barrier that precedes its first use
-  auto wait_stage = [&](int m) {
-    const int b = m % NBUF;
+  V2 wk[TPF];                    // backward: w of the current line (registers)
+  gather(line_of(0), pf);
+  bool abort = false, met = false;
+  // thread 0 waits for the block of step s before a barrier that precedes its first use
+  auto wait_stage = [&](int s) {
+    const int b = s % NBUF;
     if (tid == 0 && !s_abort && !mbar_wait(&bars[b], (phase >> b) & 1u)) {
       s_abort = 1;
       atomicExch(err, (int)MSTOPO_TIMEOUT);
@@ -362,125 +484,93 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
   };
   wait_stage(0);
   __syncthreads();
-  for (int m = 0; m < nseq; ++m) {
-    if constexpr (NBUF == 1) {   // one stage: block m was issued at the end of step m - 1
-      if (m > 0) {
-        wait_stage(m);
+  for (int s = 0; s < nseq; ++s) {
+    if constexpr (NBUF == 1) {   // one stage: block s was issued at the end of step s - 1
+      if (s > 0) {
+        wait_stage(s);
         __syncthreads();
       }
     }
     if (s_abort) { abort = true; break; }
-    const bool fw = m < NL;
-    const int k = line_of(m);
-    const int b = m % NBUF;
-    const T* L = ring + (long long)b * geo.LB;
-    const T* Bq = L + geo.TB;
-    if (fw) {
-      // t = b_k - B_k w_{k-1}
+    const T* L = ring + (long long)(s % NBUF) * geo.LBM;
+    if (s < Lc) {
+      // forward chain line j: t = b - C_j w_{j-1}, w_j = S_j^-1 t
+      const int j = s, l = line_of(j);
+      if (j > 0) {
+        couple(L + geo.TB, vp, T(-1), true, vt);
+      } else {
 #pragma unroll
-      for (int s = 0; s < TPF; ++s) {
-        const int q = tid + s * NTH;
-        if (q >= nb * RC) continue;
-        const int row = q / RC, ch = q % RC;
-        T v[VW];
-#pragma unroll
-        for (int e = 0; e < VW; ++e) v[e] = pf[s][e];
-        if (k > 0) {
-          const int cb = 2 * (row >> 1) - 2;
-#pragma unroll
-          for (int qq = 0; qq < 6; ++qq) {
-            const int c = cb + qq;
-            if (c < 0 || c >= nb) continue;
-            const T bq = Bq[qq * nb + row];
-#pragma unroll
-            for (int e = 0; e < VW; ++e) v[e] = fma(-bq, vp[c * R + ch * VW + e], v[e]);
-          }
-        }
-#pragma unroll
-        for (int e = 0; e < VW; ++e) vt[row * R + ch * VW + e] = v[e];
+        for (int q = 0; q < TPF; ++q)
+          if (qv[q]) *reinterpret_cast<V2*>(vt + qj[q] * NV + 2 * qa[q]) = pf[q];
       }
-      if (k + 1 < NL) gather(k + 1, pf);   // next line's input, in flight during the product
+      gather(j + 1 < Lc ? line_of(j + 1) : Lc, pf);   // next line's input (the middle line last)
       __syncthreads();
       product(L);
-      if (NBUF > 1 && m + 1 < nseq) wait_stage(m + 1);
+      if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
       __syncthreads();
-      // w_k = S_k^-1 t (in vy): to the work buffer for the backward sweep (w_{NL-1} stays in
-      // shared memory: the first backward line rewrites that slice with no barrier between);
-      // it becomes w_{k-1} of the next line
-      if (k + 1 < NL) {
-        T* Xk = X + (long long)k * nb * R;
-        for (int q = tid; q < nb * R; q += NTH) Xk[q] = vy[q];
-      }
+      // w_j (in vy) to the work buffer for the backward sweep (the last one stays in shared
+      // memory: the first backward line rewrites that slot); it becomes w_{j-1} of the next line
+      if (j + 1 < Lc) store_line(l, vy);
       T* tmp = vp; vp = vy; vy = tmp;
-    } else {
-      // backward line k: x_k = w_k - S_k^-1 t_k, t_k = B_{k+1}^T x_{k+1} already in vt.
-      // w_k was loaded from the work buffer in the previous step (before its barrier, so no
-      // load can see this step's x_k stores into the same slice); w_{NL-1} is still in vp.
-      const bool first = m == NL;           // t_{NL-1} = 0: x = w
-      if (first) {
+    } else if (s == Lc) {
+      // middle line: u = C_mid w_{Lc-1} published, then x_m = M^-1 (b_m - u_0 - u_1) in both CTAs
+      const T* Cown = L + geo.TB + rank * 6 * nb;
+      couple(Cown, vp, T(1), false, vu);
+      cluster.sync();   // both contributions are in shared memory
+      met = true;
+      const T* vu0 = rank == 0 ? vu : cluster.map_shared_rank(vu, 0);
+      const T* vu1 = rank == 1 ? vu : cluster.map_shared_rank(vu, 1);
 #pragma unroll
-        for (int s = 0; s < TPF; ++s) {
-          const int q = tid + s * NTH;
-          if (q >= nb * RC) continue;
-          const int row = q / RC, ch = q % RC;
-#pragma unroll
-          for (int e = 0; e < VW; ++e) wk[s][e] = vp[row * R + ch * VW + e];
-        }
-      } else {
-        product(L);
-        __syncthreads();
+      for (int q = 0; q < TPF; ++q) {
+        if (!qv[q]) continue;
+        const int o = qj[q] * NV + 2 * qa[q];
+        const V2 u0 = *reinterpret_cast<const V2*>(vu0 + o);
+        const V2 u1 = *reinterpret_cast<const V2*>(vu1 + o);
+        V2 t;
+        t.x = (pf[q].x - u0.x) - u1.x;
+        t.y = (pf[q].y - u0.y) - u1.y;
+        *reinterpret_cast<V2*>(vt + o) = t;
+        wk[q] = *reinterpret_cast<const V2*>(vp + o);   // w_{Lc-1} for the first backward line
       }
-      T* Xk = X + (long long)k * nb * R;
-#pragma unroll
-      for (int s = 0; s < TPF; ++s) {
-        const int q = tid + s * NTH;
-        if (q >= nb * RC) continue;
-        const int row = q / RC, ch = q % RC;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          const int j = ch * VW + e;
-          const T x = first ? wk[s][e] : wk[s][e] - result(row * R + j);
-          vw[row * R + j] = x;
-          Xk[(long long)j * nb + row] = x;   // [R][nb] for the combine step
-        }
-      }
-      if (k > 0) load_w(k - 1, wk);
       __syncthreads();
-      // t_{k-1} = B_k^T x_k  (column c of line k-1 gathers rows of nodes (c>>1) - 1 .. + 1)
-      if (k > 0) {
-        for (int q = tid; q < nb * RC; q += NTH) {
-          const int c = q / RC, ch = q % RC;
-          T v[VW];
+      product(L);
+      __syncthreads();
+      if (rank == 0) store_line(Lc, vy);
+      couple_t(Cown, vy, vt);   // t of chain line Lc - 1
+      if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
+      __syncthreads();
+    } else {
+      // backward chain line j: x_j = w_j - S_j^-1 t_j, then t_{j-1} = C_j^T x_j
+      const int j = 2 * Lc - s, l = line_of(j);
+      product(L);
+      __syncthreads();
 #pragma unroll
-          for (int e = 0; e < VW; ++e) v[e] = T(0);
-          const int a = c >> 1;
-          for (int an = a - 1; an <= a + 1; ++an) {
-            if (an < 0 || 2 * an >= nb) continue;
-#pragma unroll
-            for (int cr = 0; cr < 2; ++cr) {
-              const int row = 2 * an + cr;
-              const int qq = c - (2 * an - 2);
-              const T bq = Bq[qq * nb + row];
-#pragma unroll
-              for (int e = 0; e < VW; ++e) v[e] = fma(bq, vw[row * R + ch * VW + e], v[e]);
-            }
-          }
-#pragma unroll
-          for (int e = 0; e < VW; ++e) vt[c * R + ch * VW + e] = v[e];
-        }
+      for (int q = 0; q < TPF; ++q) {
+        if (!qv[q]) continue;
+        const int o = qj[q] * NV + 2 * qa[q];
+        const V2 y = *reinterpret_cast<const V2*>(vy + o);
+        V2 x;
+        x.x = wk[q].x - y.x;
+        x.y = wk[q].y - y.y;
+        *reinterpret_cast<V2*>(vw + o) = x;
+        *reinterpret_cast<V2*>(X + ((long long)l * R + qj[q]) * nb + 2 * qa[q]) = x;
       }
-      if (NBUF > 1 && m + 1 < nseq) wait_stage(m + 1);
+      if (j > 0) load_w(line_of(j - 1), wk);
+      __syncthreads();
+      if (j > 0) couple_t(L + geo.TB, vw, vt);
+      if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
       __syncthreads();
     }
-    // every read of stage b is behind a barrier: refill it with block m + NBUF
+    // every read of stage s % NBUF is behind a barrier: refill it with block s + NBUF
     if (tid == 0 && issued < nseq && !s_abort) {
-      const int st = issued % NBUF;   // == b
-      mbar_expect_tx(&bars[st], bytes);
-      bulk_g2s(ring + (long long)st * geo.LB, src + (long long)line_of(issued) * geo.LB, bytes,
+      const int st = issued % NBUF;
+      mbar_expect_tx(&bars[st], block_bytes(issued));
+      bulk_g2s(ring + (long long)st * geo.LBM, src + block_off(issued), block_bytes(issued),
                &bars[st]);
       ++issued;
     }
   }
+  if (!met) cluster.sync();   // the partner meets this CTA at the middle line in any case
   if (abort && tid == 0) {
     // every copy issued and not yet waited for lands before the CTA exits
     for (int m2 = 0; m2 < NBUF; ++m2) {
@@ -491,29 +581,41 @@ __global__ void __launch_bounds__(32 * TMAXW, MINB) k_patch_tri(
       if (!tri_wait(&bars[st], par)) atomicExch(err, (int)MSTOPO_TIMEOUT);
     }
   }
+  cluster.sync();   // the partner has read this CTA's contribution
 }
 
 // ------------------------------------------------------------------------------ host side
-static int tri_threads(int nb) { return 32 * (2 * (nb / 32) + (nb % 32 ? 1 : 0)); }
-
-size_t patch_tri_smem(int nb, int R, int nbuf, size_t elem) {
-  const TriGeom g = tri_geometry(nb);
-  return ((size_t)nbuf * g.LB + 4 * (size_t)g.NV * R) * elem;
+static int tri_threads(int nb) {
+  const int t = 32 * (2 * (nb / 32) + (nb % 32 ? 1 : 0));
+  return t < TMINTH ? TMINTH : t;
 }
 
-long long patch_tri_line_elems(int nb) { return tri_geometry(nb).LB; }
+static size_t patch_tri_smem(int nb, int R, int nbuf, size_t elem) {
+  const TriGeom g = tri_geometry(nb, 3);
+  return ((size_t)nbuf * g.LBM + 5 * (size_t)g.NV * R) * elem;
+}
+
+long long patch_tri_system_elems(int nb, int NL) { return tri_geometry(nb, NL).SS; }
+
+int patch_tri_ctas_per_sm(int nb, int R) {
+  // 228 KB of shared memory per SM, 1 KB reserved per CTA, the static arrays below 2 KB
+  const size_t per = patch_tri_smem(nb, R, 2, 4) + 3 * 1024;
+  return std::max(1, (int)((228 * 1024) / per));
+}
 
 // the kernel's thread layout covers this line size: at most 9 warps, rows addressed through
 // a 160-entry table, every vector phase within 4 pairs per thread (16 patches per CTA)
 bool patch_tri_assignment_ok(int nb) {
   const int nt = tri_threads(nb);
-  return nb >= 2 && nb <= 160 && nt <= 32 * TMAXW && nb * 4 <= 4 * nt;
+  return nb >= 2 && nb % 2 == 0 && nb <= 160 && nt <= 32 * TMAXW && (nb / 2) * 16 <= 4 * nt;
 }
 
-cudaError_t patch_tri_pack(const double* Linv, const double* B, int nsys, int nb, int NL,
-                           double* out64, float* out32, cudaStream_t s) {
-  const TriGeom g = tri_geometry(nb);
-  note_launch(), k_patch_tri_pack<<<dim3(nsys, NL), 256, 0, s>>>(Linv, B, NL, g, out64, out32);
+cudaError_t patch_tri_pack(const double* Lt, const double* Bt, const double* Lr, const double* Br,
+                           const double* Lm, int nsys, int nb, int NL, int NLr, double* out64,
+                           float* out32, cudaStream_t s) {
+  const TriGeom g = tri_geometry(nb, NL);
+  note_launch(), k_patch_tri_pack<<<dim3(nsys, NL), 256, 0, s>>>(Lt, Bt, Lr, Br, Lm, NL, NLr, g,
+                                                                 out64, out32);
   return cudaGetLastError();
 }
 
@@ -522,28 +624,29 @@ static cudaError_t launch_tri_kt(mstopo_handle* h, const PatchGroups& G, const T
                                  int nsys, const T* pack, T* Xg) {
   constexpr int MINB = (sizeof(T) == 4 && R <= 4) ? 2 : 1;   // two CTAs per SM at four columns
   Precond& pc = h->pc;
-  const TriGeom geo = tri_geometry(pc.nbP);
+  const TriGeom geo = tri_geometry(pc.nbP, pc.NP);
   const size_t sm = patch_tri_smem(pc.nbP, R, NBUF, sizeof(T));
   {
     cudaError_t e = smem_limit_max<k_patch_tri<T, R, NBUF, MINB, TPF>>();
     if (e != cudaSuccess) return e;
   }
-  if (sm > 225 * 1024 || !patch_tri_assignment_ok(pc.nbP)) return cudaErrorInvalidConfiguration;
+  if (sm > 225 * 1024 || !patch_tri_assignment_ok(pc.nbP) || pc.NP % 2 == 0)
+    return cudaErrorInvalidConfiguration;
   const int g0 = G.h_begin[sys0], ng = G.h_begin[sys0 + nsys] - g0;
   if (ng <= 0) return cudaSuccess;
-  note_launch(), k_patch_tri<T, R, NBUF, MINB, TPF><<<ng, tri_threads(pc.nbP), sm, h->s>>>(
+  note_launch(), k_patch_tri<T, R, NBUF, MINB, TPF><<<2 * ng, tri_threads(pc.nbP), sm, h->s>>>(
       r, h->n_dof, sys0, g0, h->nelx, h->nely, pc.H, pc.ncx, G.d_type, G.d_sys, G.d_first,
       G.d_count, G.d_perm, pc.d_pfree, pack, geo, Xg, h->d_flag + 1);
   return cudaGetLastError();
 }
 
-// one (row, 16-byte chunk) pair per thread when the threads cover the vector phases, else four
+// the fewest (node, right-hand side) pairs per thread that cover the vector phases
 template <typename T, int R, int NBUF>
 static cudaError_t launch_tri_k(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
                                 int nsys, const T* pack, T* Xg) {
-  const int nb = h->pc.nbP;
-  if (nb * (R * (int)sizeof(T) / 16) <= tri_threads(nb))
-    return launch_tri_kt<T, R, NBUF, 1>(h, G, r, sys0, nsys, pack, Xg);
+  const int pairs = (h->pc.nbP / 2) * R, nt = tri_threads(h->pc.nbP);
+  if (pairs <= nt) return launch_tri_kt<T, R, NBUF, 1>(h, G, r, sys0, nsys, pack, Xg);
+  if (pairs <= 2 * nt) return launch_tri_kt<T, R, NBUF, 2>(h, G, r, sys0, nsys, pack, Xg);
   return launch_tri_kt<T, R, NBUF, 4>(h, G, r, sys0, nsys, pack, Xg);
 }
 

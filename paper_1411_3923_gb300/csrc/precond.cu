@@ -232,6 +232,67 @@ __global__ void k_bt_factor(const double* __restrict__ A, const double* __restri
   if (threadIdx.x == 0) status[sys] = f;
 }
 
+// Two-sided elimination of the patch matrices (the middle line m = H meets both halves):
+// lines 0..NLr-1 of the line-reversed systems, A'_j = A_{NL-1-j},
+// B'_j = A'_{j+1,j} = (A_{NL-1-j,NL-2-j})^T = B_{NL-2-j}^T, free'_j = free_{NL-1-j}.
+__global__ void k_reverse_lines(const double* __restrict__ A, const double* __restrict__ B,
+                                const uint8_t* __restrict__ freem, int NL, int NLr, int nb,
+                                double* __restrict__ Ar, double* __restrict__ Br,
+                                uint8_t* __restrict__ fr) {
+  const int sys = blockIdx.x, j = blockIdx.y, l = NL - 1 - j;
+  const long long nn = (long long)nb * nb;
+  const double* As = A + ((long long)sys * NL + l) * nn;
+  double* Ad = Ar + ((long long)sys * NLr + j) * nn;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) Ad[t] = As[t];
+  if (j + 1 < NLr) {
+    const double* Bs = B + ((long long)sys * (NL - 1) + NL - 2 - j) * nn;
+    double* Bd = Br + ((long long)sys * (NLr - 1) + j) * nn;
+    for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+      const long long i = t / nb, c = t % nb;
+      Bd[t] = Bs[c * nb + i];
+    }
+  }
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    fr[((long long)sys * NLr + j) * nb + i] = freem[((long long)sys * NL + l) * nb + i];
+}
+
+// The middle line's Schur complement M = A_m (+ shift) - C_{m-1} C_{m-1}^T - C'_{m-1} C'_{m-1}^T
+// (C = B L^-T of the top-down factor and of the line-reversed one, m = (NL - 1) / 2), its
+// Cholesky factor in place and Lm = L_M^-1.  status[sys] = 0 or 1 + the failing pivot.
+__global__ void k_twist_middle(const double* __restrict__ A, const double* __restrict__ Ct,
+                               const double* __restrict__ Cr, const uint8_t* __restrict__ freem,
+                               double shift, int NL, int NLr, int nb, double* __restrict__ S,
+                               double* __restrict__ Lm, int* __restrict__ status) {
+  __shared__ int sh_fail;
+  __shared__ double dinv[BT_MAX_NB];
+  const int sys = blockIdx.x, m = (NL - 1) / 2;
+  const long long nn = (long long)nb * nb;
+  const double* Am = A + ((long long)sys * NL + m) * nn;
+  const double* C0 = Ct + ((long long)sys * (NL - 1) + m - 1) * nn;
+  const double* C1 = Cr + ((long long)sys * (NLr - 1) + m - 1) * nn;
+  const uint8_t* fm = freem + ((long long)sys * NL + m) * nb;
+  double* Sm = S + sys * nn;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = (int)(t / nb), l = (int)(t % nb);
+    double v = Am[t];
+    if (i == l && fm[i]) v *= (1.0 + shift);
+    if (l <= i) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int q = 0; q < nb; ++q) {
+        s0 = fma(C0[(long long)i * nb + q], C0[(long long)l * nb + q], s0);
+        s1 = fma(C1[(long long)i * nb + q], C1[(long long)l * nb + q], s1);
+      }
+      v -= s0;
+      v -= s1;
+    }
+    Sm[t] = v;
+  }
+  __syncthreads();
+  const int f = bt_chol_inplace(Sm, nb, &sh_fail, dinv);
+  bt_tri_inverse(Sm, dinv, Lm + sys * nn, nb);
+  if (threadIdx.x == 0) status[sys] = f;
+}
+
 // ------------------------------------------------------------------------------ eigen
 // Small dense helpers (thread 0 only).  Cyclic Jacobi for a symmetric q x q matrix:
 // on exit A is (numerically) diagonal and V holds the eigenvectors as columns.
@@ -1127,7 +1188,30 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const int P = std::max(1, std::min(PATCH_COLS, (pc.Nc * nsv + sms - 1) / std::max(sms, 1)));
+  // Columns per FP32 group (4, 8 or 16 patches of one type and realisation): each group is a
+  // cluster of two CTAs and patch_tri_ctas_per_sm(R) CTAs fit on an SM, so a choice costs
+  // ceil(2 groups / (ctas per SM x SMs)) waves of its per-CTA time; the time of a CTA grows
+  // with its columns (measured per wave, 1024x512 workload: R = 8 about 1.4, R = 16 about
+  // 2.4 times R = 4 with two CTAs per SM).  Fewer columns win ties.
+  int P = 4;
+  {
+    std::vector<long long> per_type(T, 0);
+    for (int i = 0; i < pc.Nc; ++i) per_type[pc.h_type_of_agg[i]]++;
+    const int cols[3] = {4, 8, 16};
+    const double cost[3] = {1.0, 1.4, 2.4};
+    double best = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      long long groups = 0;
+      for (int t = 0; t < T; ++t) groups += (per_type[t] + cols[c] - 1) / cols[c];
+      groups *= nsv;
+      const long long slots = (long long)patch_tri_ctas_per_sm(nbP, cols[c]) * std::max(sms, 1);
+      const double t = (double)((2 * groups + slots - 1) / slots) * cost[c];
+      if (c == 0 || t < best - 1e-9) {
+        best = t;
+        P = cols[c];
+      }
+    }
+  }
   if (!patch_tri_assignment_ok(nbP)) {
     h->err = "H > 32 is not supported by the patch solve";
     return MSTOPO_INVALID_ARG;
@@ -1135,16 +1219,53 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   if (!sgs) {
     const double* pLi = dLi + (size_t)T * NA * nnA;
     const double* pB = dB + (size_t)T * (NA - 1) * nnA;
-    // the CUDA-core patch solves stream Linv_k and B_k (FP64 always, FP32 unless the tensor
+    const double* pA = dA + (size_t)T * NA * nnA;
+    const double* pCt = dC + (size_t)T * (NA - 1) * nnA;
+    // two-sided elimination for the CUDA-core patch solves: the first H + 1 lines of the
+    // line-reversed patch matrices, factorised top-down, are the bottom half; the middle line
+    // H takes the Schur complements of both halves
+    const int NLr = H + 1;
+    double *dAr, *dBr, *dLr, *dCr, *dSr, *dLm;
+    uint8_t* dfr;
+    int* d_st2;
+    CKB(cudaMalloc(&dAr, (size_t)TP * NLr * nnP * 8));
+    CKB(cudaMalloc(&dBr, (size_t)TP * (NLr - 1) * nnP * 8));
+    CKB(cudaMalloc(&dLr, (size_t)TP * NLr * nnP * 8));
+    CKB(cudaMalloc(&dCr, (size_t)TP * (NLr - 1) * nnP * 8));
+    CKB(cudaMalloc(&dSr, (size_t)TP * nnP * 8));
+    CKB(cudaMalloc(&dLm, (size_t)TP * nnP * 8));
+    CKB(cudaMalloc(&dfr, (size_t)TP * NLr * nbP));
+    CKB(cudaMalloc(&d_st2, (size_t)2 * TP * sizeof(int)));
+    note_launch(), k_reverse_lines<<<dim3(TP, NLr), PC_THREADS, 0, s>>>(pA, pB, pc.d_pfree, NP, NLr, nbP,
+                                                                        dAr, dBr, dfr);
+    CKB(cudaGetLastError());
+    note_launch(), k_bt_factor<<<TP, PC_THREADS, 0, s>>>(dAr, dBr, dfr, pc.local_shift, pc.local_shift, 0,
+                                                         nbP, NLr, dLr, dCr, dSr, d_st2);
+    CKB(cudaGetLastError());
+    note_launch(), k_twist_middle<<<TP, PC_THREADS, 0, s>>>(pA, pCt, dCr, pc.d_pfree, pc.local_shift, NP,
+                                                            NLr, nbP, dSr, dLm, d_st2 + TP);
+    CKB(cudaGetLastError());
+    std::vector<int> st2(2 * (size_t)TP);
+    CKB(cudaMemcpyAsync(st2.data(), d_st2, 2 * (size_t)TP * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKB(cudaStreamSynchronize(s));
+    for (int t = 0; t < 2 * TP; ++t)
+      if (st2[t]) {
+        h->err = "patch matrix not positive definite";
+        return MSTOPO_NOT_SPD;
+      }
+    // the CUDA-core patch solves stream the packed blocks (FP64 always, FP32 unless the tensor
     // cores take the FP32 patch solves)
     // The tensor-core kernel's line has a fixed MMA chain (68 tcgen05.mma whatever the number
     // of columns): it pays off with full 16-column groups and two CTAs per SM; on small
     // problems (a few patches per SM) the CUDA-core kernel's shorter line wins.
     pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 32LL * sms);
-    const size_t tl = (size_t)TP * NP * patch_tri_line_elems(nbP);
+    const size_t tl = (size_t)TP * patch_tri_system_elems(nbP, NP);
     CKB(cudaMalloc(&pc.d_tri64, tl * 8));
     if (!pc.patch_tc) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
-    CKB(patch_tri_pack(pLi, pB, TP, nbP, NP, pc.d_tri64, pc.d_tri32, s));
+    CKB(patch_tri_pack(pLi, pB, dLr, dBr, dLm, TP, nbP, NP, NLr, pc.d_tri64, pc.d_tri32, s));
+    CKB(cudaStreamSynchronize(s));
+    cudaFree(dAr); cudaFree(dBr); cudaFree(dLr); cudaFree(dCr); cudaFree(dSr); cudaFree(dLm);
+    cudaFree(dfr); cudaFree(d_st2);
     if (pc.patch_tc) {
       // tensor-core FP32 line pack: [Linv_k | -W_k], [Linv_k^T | -V_k]
       const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
