@@ -35,15 +35,17 @@
 // Per patch system: chain blocks of rank 0 (lines 0..H-1), of rank 1 (lines NL-1..H+1), then
 // the middle block.
 //
-// Product y = S^-1 t: each warp owns 16 rows of a full row block I (lane = row, two lanes
-// per row splitting the reduction) and forms them completely: the chunks (I, J <= I) along
-// the rows (pairs of columns), the chunks (J' > I, I) below them down their columns (pairs of
-// rows), and the partial block's rows; the partial sums of even and odd columns are carried
-// as pairs (one paired FP32 FMA per matrix pair and right-hand side).  Every row block costs
-// the same nfull chunks, so the warps are balanced and no partial sums cross warps.  One more
-// warp forms the partial block's complete rows (lanes over column pairs, warp reduction in a
-// fixed order).  Vectors are [R][NV] in shared memory; the vector phases map one thread to a
-// (node, right-hand side) pair.  The results are bitwise repeatable.
+// Product y = S^-1 t: two warps own the 32 rows of a full row block I (each lane two rows,
+// 16 apart, two lanes per row pair splitting the reduction, so every vector load feeds two
+// rows) and form them completely: the chunks (I, J <= I) along the rows (pairs of columns),
+// the chunks (J' > I, I) below them down their columns (pairs of rows), and the partial
+// block's rows, split between the two warps, which add their sums behind a barrier of the
+// pair.  The partial sums of even and odd columns are carried as pairs (one paired FP32 FMA
+// per matrix pair and right-hand side).  Every row block costs the same nfull chunks, so the
+// warp pairs are balanced.  One more warp forms the partial block's complete rows (lanes over
+// column pairs, warp reduction in a fixed order).  Vectors are [R][NV] in shared memory; the
+// vector phases map one thread to a (node, right-hand side) pair.  The results are bitwise
+// repeatable.
 //
 // The two CTAs meet once, at the middle line: each publishes its coupling contribution in its
 // own shared memory, both cross a cluster barrier, and both form x_m from the two
@@ -80,6 +82,18 @@ template <> struct Pair<double> { using type = double2; };
 __device__ __forceinline__ float2 fma_pair(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ double2 fma_pair(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// barrier of the two warps that share row block I (ids 1..5; id 0 is __syncthreads), with
+// constant ids so that the CTA reserves six barriers only
+__device__ __forceinline__ void pair_barrier(int I) {
+  switch (I) {
+    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    case 3: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 5, 64;" ::: "memory"); break;
+  }
 }
 
 // four consecutive T as two pairs (16-byte aligned)
@@ -229,6 +243,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
   T* vw = vy + NV * R;                                    // [R][NV] x of the current line
   T* vp = vw + NV * R;                                    // [R][NV] w of the previous line
   T* vu = vp + NV * R;                                    // [R][NV] this CTA's middle contribution
+  T* vq = vu + NV * R;                                    // [R][NV] partial sums of the product
 
   if (tid < 16) {
     int ox = 0, oy = 0;
@@ -247,7 +262,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero the vectors (rows nb..NV-1 stay zero for the whole solve)
-  for (int q = tid; q < 5 * NV * R; q += NTH) vt[q] = T(0);
+  for (int q = tid; q < 6 * NV * R; q += NTH) vt[q] = T(0);
   __syncthreads();
 
   // ---- block stream: s = 0 .. 2 Lc; s < Lc forward chain line s, s = Lc the middle line,
@@ -326,12 +341,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
       t.y = with_base ? pf[s].y : T(0);
       const T* wj = w + jj * NV;
 #pragma unroll
-      for (int qq = 0; qq < 6; ++qq) {
-        const int c = 2 * a - 2 + qq;
-        if (c < 0 || c >= nb) continue;
-        const T wv = sign * wj[c];
-        t.x = fma(C[qq * nb + 2 * a], wv, t.x);
-        t.y = fma(C[qq * nb + 2 * a + 1], wv, t.y);
+      for (int dn = -1; dn <= 1; ++dn) {
+        // node n = a + dn: its columns 2n, 2n + 1 are entries q0, q0 + 1 of rows 2a, 2a + 1
+        const int n = a + dn;
+        if (n < 0 || n >= NN) continue;
+        const int q0 = 2 + 2 * dn;
+        const V2 wv = *reinterpret_cast<const V2*>(wj + 2 * n);
+        const V2 c0 = *reinterpret_cast<const V2*>(C + q0 * nb + 2 * a);
+        const V2 c1 = *reinterpret_cast<const V2*>(C + (q0 + 1) * nb + 2 * a);
+        const T w0 = sign * wv.x, w1 = sign * wv.y;
+        t.x = fma(c0.x, w0, t.x);
+        t.y = fma(c0.y, w0, t.y);
+        t.x = fma(c1.x, w1, t.x);
+        t.y = fma(c1.y, w1, t.y);
       }
       *reinterpret_cast<V2*>(out + jj * NV + 2 * a) = t;
     }
@@ -364,72 +386,107 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
     }
   };
 
-  // vy = S^-1 vt.  Row warp w owns rows 16 w .. 16 w + 15 (row block I = w / 2); lane
-  // i + 16 h takes row 16 w + i and half h of every reduction.
+  // vy = S^-1 vt.  Warps 2I and 2I + 1 share the 32 rows of row block I: lane i + 16 h takes
+  // rows 32 I + i and 32 I + i + 16 and half h of every reduction (each vector load feeds both
+  // rows); the block's nfull chunks are split between the two warps (the first half of the
+  // list (I, 0), .., (I, I), (I + 1, I), .., (nfull - 1, I) to warp 2I, the rest and the
+  // partial block's rows to warp 2I + 1), which add their sums through vq behind a barrier of
+  // the pair.
   auto product = [&](const T* L) {
     if (warp < nrw) {
-      const int I = warp >> 1, i = lane & 15, h = lane >> 4;
-      const int row = 16 * warp + i;
-      const int col = row - 32 * I;              // the row's column inside chunks (J' > I, I)
-      V2 acc[R];                                 // (even, odd) columns of every right-hand side
+      const int I = warp >> 1, side = warp & 1, i = lane & 15, h = lane >> 4;
+      const int r0 = 32 * I + i;                 // rows r0 and r0 + 16 (columns i, i + 16 of chunks (J', I))
+      const int half = (nfull + 1) >> 1;
+      V2 acc0[R], acc1[R];                       // (even, odd) columns of every right-hand side
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        acc[j].x = T(0);
-        acc[j].y = T(0);
+        acc0[j].x = T(0); acc0[j].y = T(0);
+        acc1[j].x = T(0); acc1[j].y = T(0);
       }
-      // chunks (I, J <= I) along the row: columns 32 J + 16 h .. + 15, by pairs
-      const T* Lr = L + s_rowoff[row] + 16 * h;
-      for (int J = 0; J <= I; ++J) {
-        const T* Lc_ = Lr + 32 * J;
-        const T* tv = vt + 32 * J + 16 * h;
+      const int k1 = side ? nfull : half;
+      for (int k = side ? half : 0; k < k1; ++k) {
+        if (k <= I) {
+          // chunk (I, k) along rows r0, r0 + 16: columns 32 k + 16 h .. + 15, by pairs
+          const T* L0 = L + s_rowoff[r0] + 32 * k + 16 * h;
+          const T* L1 = L + s_rowoff[r0 + 16] + 32 * k + 16 * h;
+          const T* tv = vt + 32 * k + 16 * h;
 #pragma unroll
-        for (int c = 0; c < 16; c += 4) {
-          const V2 m01 = *reinterpret_cast<const V2*>(Lc_ + c);
-          const V2 m23 = *reinterpret_cast<const V2*>(Lc_ + c + 2);
+          for (int c = 0; c < 16; c += 4) {
+            const V2 a01 = *reinterpret_cast<const V2*>(L0 + c);
+            const V2 a23 = *reinterpret_cast<const V2*>(L0 + c + 2);
+            const V2 b01 = *reinterpret_cast<const V2*>(L1 + c);
+            const V2 b23 = *reinterpret_cast<const V2*>(L1 + c + 2);
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
-            V2 v01, v23;
-            ld_quad<T, V2>(tv + j * NV + c, v01, v23);
-            acc[j] = fma_pair(m01, v01, acc[j]);
-            acc[j] = fma_pair(m23, v23, acc[j]);
+            for (int j = 0; j < R; ++j) {
+              V2 v01, v23;
+              ld_quad<T, V2>(tv + j * NV + c, v01, v23);
+              acc0[j] = fma_pair(a01, v01, acc0[j]);
+              acc1[j] = fma_pair(b01, v01, acc1[j]);
+              acc0[j] = fma_pair(a23, v23, acc0[j]);
+              acc1[j] = fma_pair(b23, v23, acc1[j]);
+            }
+          }
+        } else {
+          // chunk (k, I) down columns i and i + 16: half h takes the rows 32 k + {0..7, 16..23}
+          // + 8 h (8 rows apart, the two halves read disjoint banks), by pairs of rows
+          const int S2 = 32 * (k + 1) + 2;                      // row stride of block k
+          const T* La = L + s_rowoff[32 * k + 8 * h] + 32 * I + i;
+          const T* ta = vt + 32 * k + 8 * h;
+#pragma unroll
+          for (int g4 = 0; g4 < 4; ++g4) {
+            const int dr = (g4 & 1) * 4 + (g4 >> 1) * 16;       // 0, 4, 16, 20
+            V2 a01, a23, b01, b23;
+            a01.x = La[dr * S2];            a01.y = La[(dr + 1) * S2];
+            a23.x = La[(dr + 2) * S2];      a23.y = La[(dr + 3) * S2];
+            b01.x = La[dr * S2 + 16];       b01.y = La[(dr + 1) * S2 + 16];
+            b23.x = La[(dr + 2) * S2 + 16]; b23.y = La[(dr + 3) * S2 + 16];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              V2 v01, v23;
+              ld_quad<T, V2>(ta + j * NV + dr, v01, v23);
+              acc0[j] = fma_pair(a01, v01, acc0[j]);
+              acc1[j] = fma_pair(b01, v01, acc1[j]);
+              acc0[j] = fma_pair(a23, v23, acc0[j]);
+              acc1[j] = fma_pair(b23, v23, acc1[j]);
+            }
           }
         }
       }
-      // chunks (J' > I, I) down column `col`: half h takes the rows 32 J' + {0..7, 16..23} + 8 h
-      // (8 rows apart, the two halves read disjoint banks), by pairs of rows
-      for (int J2 = I + 1; J2 < nfull; ++J2) {
-        const int S2 = 32 * (J2 + 1) + 2;                       // row stride of block J2
-        const T* La = L + s_rowoff[32 * J2 + 8 * h] + 32 * I + col;
-        const T* ta = vt + 32 * J2 + 8 * h;
-#pragma unroll
-        for (int g4 = 0; g4 < 4; ++g4) {
-          const int dr = (g4 & 1) * 4 + (g4 >> 1) * 16;         // 0, 4, 16, 20
-          V2 m01, m23;
-          m01.x = La[dr * S2];
-          m01.y = La[(dr + 1) * S2];
-          m23.x = La[(dr + 2) * S2];
-          m23.y = La[(dr + 3) * S2];
+      if (side) {
+        // the partial block's rows (complete rows stored): columns r0, r0 + 16 of each
+        for (int e = h; e < rem; e += 2) {
+          const int rw = 32 * nfull + e;
+          const T a0 = L[s_rowoff[rw] + r0], a1 = L[s_rowoff[rw] + r0 + 16];
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            V2 v01, v23;
-            ld_quad<T, V2>(ta + j * NV + dr, v01, v23);
-            acc[j] = fma_pair(m01, v01, acc[j]);
-            acc[j] = fma_pair(m23, v23, acc[j]);
+            const T v = vt[j * NV + rw];
+            acc0[j].x = fma(a0, v, acc0[j].x);
+            acc1[j].x = fma(a1, v, acc1[j].x);
           }
         }
       }
-      // the partial block's rows (complete rows stored): column `row` of each
-      for (int e = h; e < rem; e += 2) {
-        const int rw = 32 * nfull + e;
-        const T a = L[s_rowoff[rw] + row];
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[j].x = fma(a, vt[j * NV + rw], acc[j].x);
-      }
+      T s0[R], s1[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        T s = acc[j].x + acc[j].y;
-        s += __shfl_xor_sync(0xffffffffu, s, 16);
-        if (h == 0) vy[j * NV + row] = s;
+        s0[j] = acc0[j].x + acc0[j].y;
+        s1[j] = acc1[j].x + acc1[j].y;
+        s0[j] += __shfl_xor_sync(0xffffffffu, s0[j], 16);
+        s1[j] += __shfl_xor_sync(0xffffffffu, s1[j], 16);
+      }
+      if (side && h == 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          vq[j * NV + r0] = s0[j];
+          vq[j * NV + r0 + 16] = s1[j];
+        }
+      }
+      pair_barrier(I);   // warp 2I + 1's sums are in vq
+      if (!side && h == 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          vy[j * NV + r0] = s0[j] + vq[j * NV + r0];
+          vy[j * NV + r0 + 16] = s1[j] + vq[j * NV + r0 + 16];
+        }
       }
     } else if (warp == nrw && rem > 0) {
       // complete rows of the partial block: lanes over column pairs
@@ -585,6 +642,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
 }
 
 // ------------------------------------------------------------------------------ host side
+// Stages of the block ring and CTAs per SM of a launch: FP32 at four columns streams one stage
+// and runs three CTAs per SM (about 66 KB of shared memory and 72 registers each: the 318 CTAs
+// of the 1024x512 workload in one wave, each CTA's copy wait covered by the other two); more
+// columns stream two stages at one CTA per SM; FP64 one stage at one CTA per SM.
+template <typename T, int R> struct TriCfg {
+  static constexpr int NBUF = (sizeof(T) == 4 && R > 4) ? 2 : 1;
+  static constexpr int MINB = (sizeof(T) == 4 && R <= 4) ? 3 : 1;
+};
+
 static int tri_threads(int nb) {
   const int t = 32 * (2 * (nb / 32) + (nb % 32 ? 1 : 0));
   return t < TMINTH ? TMINTH : t;
@@ -592,15 +658,18 @@ static int tri_threads(int nb) {
 
 static size_t patch_tri_smem(int nb, int R, int nbuf, size_t elem) {
   const TriGeom g = tri_geometry(nb, 3);
-  return ((size_t)nbuf * g.LBM + 5 * (size_t)g.NV * R) * elem;
+  return ((size_t)nbuf * g.LBM + 6 * (size_t)g.NV * R) * elem;
 }
 
 long long patch_tri_system_elems(int nb, int NL) { return tri_geometry(nb, NL).SS; }
 
 int patch_tri_ctas_per_sm(int nb, int R) {
-  // 228 KB of shared memory per SM, 1 KB reserved per CTA, the static arrays below 2 KB
-  const size_t per = patch_tri_smem(nb, R, 2, 4) + 3 * 1024;
-  return std::max(1, (int)((228 * 1024) / per));
+  // 228 KB of shared memory per SM, 1 KB reserved per CTA, the static arrays below 2 KB;
+  // registers allow the launch bound's CTAs per SM
+  const int nbuf = R <= 4 ? TriCfg<float, 4>::NBUF : TriCfg<float, 8>::NBUF;
+  const int minb = R <= 4 ? TriCfg<float, 4>::MINB : TriCfg<float, 8>::MINB;
+  const size_t per = patch_tri_smem(nb, R, nbuf, 4) + 3 * 1024;
+  return std::max(1, std::min(minb, (int)((228 * 1024) / per)));
 }
 
 // the kernel's thread layout covers this line size: at most 9 warps, rows addressed through
@@ -619,10 +688,10 @@ cudaError_t patch_tri_pack(const double* Lt, const double* Bt, const double* Lr,
   return cudaGetLastError();
 }
 
-template <typename T, int R, int NBUF, int TPF>
+template <typename T, int R, int TPF>
 static cudaError_t launch_tri_kt(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
                                  int nsys, const T* pack, T* Xg) {
-  constexpr int MINB = (sizeof(T) == 4 && R <= 4) ? 2 : 1;   // two CTAs per SM at four columns
+  constexpr int NBUF = TriCfg<T, R>::NBUF, MINB = TriCfg<T, R>::MINB;
   Precond& pc = h->pc;
   const TriGeom geo = tri_geometry(pc.nbP, pc.NP);
   const size_t sm = patch_tri_smem(pc.nbP, R, NBUF, sizeof(T));
@@ -641,22 +710,22 @@ static cudaError_t launch_tri_kt(mstopo_handle* h, const PatchGroups& G, const T
 }
 
 // the fewest (node, right-hand side) pairs per thread that cover the vector phases
-template <typename T, int R, int NBUF>
+template <typename T, int R>
 static cudaError_t launch_tri_k(mstopo_handle* h, const PatchGroups& G, const T* r, int sys0,
                                 int nsys, const T* pack, T* Xg) {
   const int pairs = (h->pc.nbP / 2) * R, nt = tri_threads(h->pc.nbP);
-  if (pairs <= nt) return launch_tri_kt<T, R, NBUF, 1>(h, G, r, sys0, nsys, pack, Xg);
-  if (pairs <= 2 * nt) return launch_tri_kt<T, R, NBUF, 2>(h, G, r, sys0, nsys, pack, Xg);
-  return launch_tri_kt<T, R, NBUF, 4>(h, G, r, sys0, nsys, pack, Xg);
+  if (pairs <= nt) return launch_tri_kt<T, R, 1>(h, G, r, sys0, nsys, pack, Xg);
+  if (pairs <= 2 * nt) return launch_tri_kt<T, R, 2>(h, G, r, sys0, nsys, pack, Xg);
+  return launch_tri_kt<T, R, 4>(h, G, r, sys0, nsys, pack, Xg);
 }
 
 cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
                                 int nsys, float* Xg) {
   const float* pack = h->pc.d_tri32;
   switch (patch_tri_cols(G.P)) {
-    case 4: return launch_tri_k<float, 4, 2>(h, G, r, sys0, nsys, pack, Xg);
-    case 8: return launch_tri_k<float, 8, 2>(h, G, r, sys0, nsys, pack, Xg);
-    default: return launch_tri_k<float, 16, 2>(h, G, r, sys0, nsys, pack, Xg);
+    case 4: return launch_tri_k<float, 4>(h, G, r, sys0, nsys, pack, Xg);
+    case 8: return launch_tri_k<float, 8>(h, G, r, sys0, nsys, pack, Xg);
+    default: return launch_tri_k<float, 16>(h, G, r, sys0, nsys, pack, Xg);
   }
 }
 
@@ -664,7 +733,7 @@ cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const do
                                 int nsys, double* Xg) {
   const double* pack = h->pc.d_tri64;
   switch (patch_tri_cols(G.P)) {
-    case 4: return launch_tri_k<double, 4, 1>(h, G, r, sys0, nsys, pack, Xg);
+    case 4: return launch_tri_k<double, 4>(h, G, r, sys0, nsys, pack, Xg);
     default: return cudaErrorInvalidConfiguration;   // FP64 groups hold at most 4 patches
   }
 }

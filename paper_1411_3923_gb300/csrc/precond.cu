@@ -1189,16 +1189,16 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   // Columns per FP32 group (4, 8 or 16 patches of one type and realisation): each group is a
-  // cluster of two CTAs and patch_tri_ctas_per_sm(R) CTAs fit on an SM, so a choice costs
-  // ceil(2 groups / (ctas per SM x SMs)) waves of its per-CTA time; the time of a CTA grows
-  // with its columns (measured per wave, 1024x512 workload: R = 8 about 1.4, R = 16 about
-  // 2.4 times R = 4 with two CTAs per SM).  Fewer columns win ties.
+  // cluster of two CTAs and patch_tri_ctas_per_sm(R) CTAs fit on an SM (3 at R = 4, 1 above),
+  // so a choice costs ceil(2 groups / (CTAs per SM x SMs)) waves of its time per wave.
+  // Measured on the 1024x512 workload (time per wave relative to a full R = 4 wave, three CTAs
+  // per SM): R = 8 0.77, R = 16 1.44.  Fewer columns win ties.
   int P = 4;
   {
     std::vector<long long> per_type(T, 0);
     for (int i = 0; i < pc.Nc; ++i) per_type[pc.h_type_of_agg[i]]++;
     const int cols[3] = {4, 8, 16};
-    const double cost[3] = {1.0, 1.4, 2.4};
+    const double cost[3] = {1.0, 0.77, 1.44};
     double best = 0.0;
     for (int c = 0; c < 3; ++c) {
       long long groups = 0;
