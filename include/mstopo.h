@@ -187,10 +187,14 @@ mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* 
 mstopo_status mstopo_solve_host(mstopo_handle* h, int32_t realisation, const double* f,
                                 double* u, const double* u0, mstopo_solve_info* infos);
 
-/* Batches of independent instances (for example meshes of uneven sizes): the instances'
- * calls run concurrently, each on its own handle and stream from its own host
- * thread (at most 16 threads), so their kernels overlap on the GPU.  Handles must be
- * distinct and should not share a stream (a shared stream serialises them).
+/* Batches of independent instances (for example meshes of uneven sizes), each on its own
+ * handle and stream, so their kernels overlap on the GPU.  Handles must be distinct and
+ * should not share a stream (a shared stream serialises them).  The builds run from up to
+ * 16 host threads (a build waits for the GPU between its steps).  The solves run from the
+ * calling thread alone: every instance's whole solve (one CUDA graph launch with device-side
+ * convergence tests) is enqueued first, then the instances are finished in turn, so the
+ * batch is one launch sequence with one wait per instance at its end.  Handles with graphs
+ * off or per-kernel profiling on solve one after the other.
  * mstopo_batch_build_preconditioner: as mstopo_build_preconditioner(hs[b], ref, infos + b)
  *   for every b; infos: HOST array of n, may be NULL.
  * mstopo_batch_solve: as mstopo_solve(hs[b], -1, f[b], u[b], NULL, infos + 4 b) for every

@@ -277,8 +277,13 @@ mstopo_status mstopo_build_preconditioner(mstopo_handle* h, int32_t ref, mstopo_
   return st;
 }
 
-mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* f, double* u,
-                           const double* u0, mstopo_solve_info* infos) {
+}  // extern "C"
+
+// mstopo_solve in two halves (see fcg_start / fcg_finish): the start validates, applies the
+// basis update rule, enqueues the solve and the copies for mstopo_compliance_and_sensitivity;
+// the finish waits and reports.
+static mstopo_status solve_start(mstopo_handle* h, int32_t realisation, const double* f, double* u,
+                                 const double* u0) {
   if (!h) return MSTOPO_INVALID_ARG;
   if (!h->design_ready || !h->pc.built) { h->err = "design or preconditioner missing"; return MSTOPO_NOT_READY; }
   CHECK_ARG(f && u, "null pointer");
@@ -290,22 +295,39 @@ mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* 
     mstopo_status sb = mstopo_build_preconditioner(h, -1, nullptr);
     if (sb != MSTOPO_OK) return sb;
   }
+  if (realisation < 0) h->u_all_ready = 0;
+  mstopo_status st = fcg_start(h, sys0, nsys, f, u, u0);
+  if (st != MSTOPO_OK) return st;
+  if (realisation < 0) {
+    CKA(cudaMemcpyAsync(h->d_u_all, u, (size_t)nsys * h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
+    CKA(cudaMemcpyAsync(h->d_f_all, f, (size_t)h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
+  }
+  return MSTOPO_OK;
+}
+
+static mstopo_status solve_finish(mstopo_handle* h, int32_t realisation, mstopo_solve_info* infos) {
+  const int nsys = realisation < 0 ? h->n_eta : 1;
+  const bool policy = realisation < 0 && h->p.reuse_preconditioner && h->p.rebuild_ratio > 0.0;
   mstopo_solve_info local[MSTOPO_MAX_SYS];
   mstopo_solve_info* inf = infos ? infos : local;
-  mstopo_status st = fcg_solve(h, sys0, nsys, f, u, u0, inf);
+  mstopo_status st = fcg_finish(h, inf);
   if (policy && st == MSTOPO_OK) {
     int it = 0;
     for (int k = 0; k < nsys; ++k) it = std::max(it, (int)inf[k].iterations);
     if (h->base_iters < 0) h->base_iters = it;
     else if (it > h->p.rebuild_ratio * h->base_iters) h->rebuild_pending = 1;
   }
-  if (realisation < 0) {
-    CKA(cudaMemcpyAsync(h->d_u_all, u, (size_t)nsys * h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
-    CKA(cudaMemcpyAsync(h->d_f_all, f, (size_t)h->n_dof * 8, cudaMemcpyDeviceToDevice, h->s));
-    CKA(cudaStreamSynchronize(h->s));
-    h->u_all_ready = (st == MSTOPO_OK) ? 1 : 0;
-  }
+  if (realisation < 0) h->u_all_ready = (st == MSTOPO_OK) ? 1 : 0;
   return st;
+}
+
+extern "C" {
+
+mstopo_status mstopo_solve(mstopo_handle* h, int32_t realisation, const double* f, double* u,
+                           const double* u0, mstopo_solve_info* infos) {
+  mstopo_status st = solve_start(h, realisation, f, u, u0);
+  if (st != MSTOPO_OK) return st;
+  return solve_finish(h, realisation, infos);
 }
 
 mstopo_status mstopo_solve_host(mstopo_handle* h, int32_t realisation, const double* f, double* u,
@@ -550,11 +572,19 @@ mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const doub
   mstopo_status st0 = check_batch(hs, n);
   if (st0 != MSTOPO_OK) return st0;
   if (!f || !u) return MSTOPO_INVALID_ARG;
+  // One host thread: every instance's solve is enqueued on its own stream first (with the
+  // device-side loop each is a few launches and one graph launch, none waiting for the GPU),
+  // then each is finished in turn; the GPU runs the instances concurrently meanwhile.
   std::vector<mstopo_status> st(n, MSTOPO_OK);
-  run_batch(hs, n, [&](int b) {
-    st[b] = mstopo_solve(hs[b], -1, f[b], u[b], nullptr,
-                         infos ? infos + (size_t)b * MSTOPO_MAX_SYS : nullptr);
-  });
+  for (int b = 0; b < n; ++b) {
+    cudaSetDevice(hs[b]->device);
+    st[b] = solve_start(hs[b], -1, f[b], u[b], nullptr);
+  }
+  for (int b = 0; b < n; ++b) {
+    if (st[b] != MSTOPO_OK) continue;
+    cudaSetDevice(hs[b]->device);
+    st[b] = solve_finish(hs[b], -1, infos ? infos + (size_t)b * MSTOPO_MAX_SYS : nullptr);
+  }
   for (int b = 0; b < n; ++b)
     if (st[b] != MSTOPO_OK) return st[b];
   return MSTOPO_OK;

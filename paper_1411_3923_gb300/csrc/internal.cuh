@@ -197,6 +197,11 @@ struct Solver {
   FcgScalars* sc = nullptr;         // [MAX_SYS]
   FcgScalars* h_sc = nullptr;       // pinned host mirror
   int* loopstat = nullptr;          // [2] device-side loop passes, true-residual passes
+  // a solve in flight (fcg_start .. fcg_finish): its outputs land in pinned host memory
+  double* h_comp = nullptr;         // pinned [MAX_SYS] compliances, then [3] ints: loop passes, werr
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int run_sys0 = 0, run_nsys = 0, run_looped = 0, run_pending = 0;
+  int run_repl[MSTOPO_MAX_SYS] = {0};
 };
 
 struct mstopo_handle {
@@ -270,6 +275,12 @@ cudaError_t precond_apply_f32(mstopo_handle* h, const float* r, float* z, int sy
 // krylov.cu
 mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
                         const double* u0, mstopo_solve_info* infos);
+// The same solve in two halves: fcg_start enqueues it on the handle's stream (with the
+// device-side loop it returns before the solve ends; the host-driven loop runs to its end),
+// fcg_finish waits for the stream and reports.  Every fcg_start is followed by fcg_finish.
+mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
+                        const double* u0);
+mstopo_status fcg_finish(mstopo_handle* h, mstopo_solve_info* infos);
 mstopo_status solver_alloc(mstopo_handle* h);
 void solver_free(Solver& sv);
 

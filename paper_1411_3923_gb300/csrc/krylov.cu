@@ -317,6 +317,27 @@ __global__ void k_fcg_after_true(FcgScalars* sc, const double* __restrict__ rr_t
   loopstat[1] += 1;
 }
 
+// Start of the device-side loop: reference residual for the reliable updates, done flags
+// (systems already within the tolerance; a zero load is reported as INVALID_ARG), and the
+// WHILE condition (no pass at all when every system is done).
+__global__ void k_fcg_loop_init(FcgScalars* sc, int nsys, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0) return;
+  int more = 0;
+  for (int s = 0; s < nsys; ++s) {
+    FcgScalars& c = sc[s];
+    c.rr_last = c.rr;
+    c.repl = 0;
+    c.done = c.active ? 0 : 1;
+    if (c.ff == 0.0) {
+      c.status = MSTOPO_INVALID_ARG;
+      c.done = 1;
+      c.active = 0;
+    }
+    if (!c.done) more = 1;
+  }
+  cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
 // WHILE condition: some system still iterating and no bounded device wait gave up (which
 // stops every system with that status).
 __global__ void k_fcg_continue(FcgScalars* sc, int nsys, const int* __restrict__ werr,
@@ -365,6 +386,9 @@ mstopo_status solver_alloc(mstopo_handle* h) {
   CK(cudaMalloc(&sv.sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
   CK(cudaMallocHost(&sv.h_sc, MSTOPO_MAX_SYS * sizeof(FcgScalars)));
   CK(cudaMalloc(&sv.loopstat, 2 * sizeof(int)));
+  CK(cudaMallocHost(&sv.h_comp, MSTOPO_MAX_SYS * 8 + 4 * sizeof(int)));
+  CK(cudaEventCreate(&sv.ev0));
+  CK(cudaEventCreate(&sv.ev1));
   return MSTOPO_OK;
 }
 
@@ -374,6 +398,9 @@ void solver_free(Solver& sv) {
   cudaFree(sv.p32); cudaFree(sv.q32); cudaFree(sv.z32); cudaFree(sv.r32);
   cudaFree(sv.partials); cudaFree(sv.sc); cudaFree(sv.loopstat);
   if (sv.h_sc) cudaFreeHost(sv.h_sc);
+  if (sv.h_comp) cudaFreeHost(sv.h_comp);
+  if (sv.ev0) cudaEventDestroy(sv.ev0);
+  if (sv.ev1) cudaEventDestroy(sv.ev1);
   sv = Solver();
 }
 
@@ -407,18 +434,16 @@ static mstopo_status precond(mstopo_handle* h, int sys0, int nsys) {
   return MSTOPO_OK;
 }
 
-mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
-                        const double* u0, mstopo_solve_info* infos) {
+mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
+                        const double* u0) {
   Solver& sv = h->sv;
   mstopo_status st = solver_alloc(h);
   if (st != MSTOPO_OK) return st;
   const long long n = sv.n;
   const bool mixed = h->p.precision != MSTOPO_FP64;
   const double tol2 = h->p.tol * h->p.tol;
-  cudaEvent_t ev0, ev1;
-  CK(cudaEventCreate(&ev0));
-  CK(cudaEventCreate(&ev1));
-  CK(cudaEventRecord(ev0, h->s));
+  sv.run_pending = 0;
+  CK(cudaEventRecord(sv.ev0, h->s));
   CK(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), h->s));   // device-wait timeout word
   // f (same load for every system), masked; x0
   for (int s = 0; s < nsys; ++s) CK(launch_mask_copy(f, sv.f + s * n, h->d_nmask, h->n_nodes, 1, n, h->s));
@@ -439,18 +464,8 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
   if (st != MSTOPO_OK) return st;
   note_launch(), k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 1, tol2);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
-  double rr_last[MSTOPO_MAX_SYS];
+  double rr_last[MSTOPO_MAX_SYS] = {0};
   int done[MSTOPO_MAX_SYS] = {0}, repl[MSTOPO_MAX_SYS] = {0};
-  for (int s = 0; s < nsys; ++s) {
-    rr_last[s] = sv.h_sc[s].rr;
-    if (sv.h_sc[s].ff == 0.0) {
-      h->err = "zero load vector";
-      return MSTOPO_INVALID_ARG;
-    }
-    if (!sv.h_sc[s].active) done[s] = 1;
-  }
   const float* E32 = h->d_E32 + (long long)sys0 * h->n_el;
   const double* E64 = h->d_E64 + (long long)sys0 * h->n_el;
   // one flexible-CG iteration for all systems (kernels skip finished systems)
@@ -503,7 +518,7 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
       if (e != cudaSuccess) return e;
       struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{top};
       cudaGraphConditionalHandle wh, ih;
-      if ((e = cudaGraphConditionalHandleCreate(&wh, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+      if ((e = cudaGraphConditionalHandleCreate(&wh, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
       if ((e = cudaGraphConditionalHandleCreate(&ih, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
       // (the params struct holds a union without a default constructor: zeroed storage)
       alignas(cudaGraphNodeParams) unsigned char wbuf[sizeof(cudaGraphNodeParams)] = {};
@@ -512,8 +527,26 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
       wp.conditional.handle = wh;
       wp.conditional.type = cudaGraphCondTypeWhile;
       wp.conditional.size = 1;
-      cudaGraphNode_t wnode;
-      if ((e = cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp)) != cudaSuccess) return e;
+      // the loop's start (done flags, reference residuals, the WHILE condition), then the node
+      if ((e = cudaStreamBeginCaptureToGraph(h->s, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+      k_fcg_loop_init<<<1, 32, 0, h->s>>>(sv.sc, nsys, wh);
+      cudaGraphNode_t wnode = nullptr;
+      {
+        cudaError_t ce0 = cudaGetLastError();
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cgraph;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if (ce0 == cudaSuccess) ce0 = cudaStreamGetCaptureInfo(h->s, &cst, nullptr, &cgraph, &deps, nullptr, &nd);
+        if (ce0 == cudaSuccess) ce0 = cudaGraphAddNode(&wnode, cgraph, deps, nullptr, nd, &wp);
+        if (ce0 == cudaSuccess)
+          ce0 = cudaStreamUpdateCaptureDependencies(h->s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        cudaGraph_t captured0 = nullptr;
+        cudaError_t ee0 = cudaStreamEndCapture(h->s, &captured0);
+        if (ce0 != cudaSuccess) return ce0;
+        if (ee0 != cudaSuccess) return ee0;
+      }
       cudaGraph_t body = wp.conditional.phGraph_out[0];
       const long long l0 = g_launch_count.load();
       // loop body: one iteration, the check, the IF node, the continue kernel
@@ -581,32 +614,27 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
       }
     }
   }
-  int n_open = 0;
-  for (int s = 0; s < nsys; ++s) n_open += !done[s];
-  if (n_open == 0) {
-    looped = true;   // every system already within the tolerance: no iteration at all
-  } else if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed && h->fcg_graph.loop) {
-    FcgGraph& gr = h->fcg_graph;
+  int* h_ints = reinterpret_cast<int*>(sv.h_comp + MSTOPO_MAX_SYS);   // loop passes [2], werr
+  if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed && h->fcg_graph.loop) {
+    // one graph launch; nothing returns to the host before fcg_finish
     looped = true;
     h->device_loop_solves++;
-    for (int s = 0; s < nsys; ++s) {
-      sv.h_sc[s].rr_last = rr_last[s];
-      sv.h_sc[s].done = done[s];
-      sv.h_sc[s].repl = 0;
-    }
-    CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
     CK(cudaMemsetAsync(sv.loopstat, 0, 2 * sizeof(int), h->s));
-    CK(cudaGraphLaunch(gr.loop, h->s));
-    int ls[2] = {0, 0}, werr = 0;
+    CK(cudaGraphLaunch(h->fcg_graph.loop, h->s));
     CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaMemcpyAsync(ls, sv.loopstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaMemcpyAsync(&werr, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h_ints, sv.loopstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h_ints + 2, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  } else {
+    // host-driven loop: the starting state comes back first
+    CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
-    g_launch_count.fetch_add((long long)ls[0] * gr.loop_launches + (long long)ls[1] * gr.true_launches);
     for (int s = 0; s < nsys; ++s) {
-      done[s] = 1;
-      repl[s] = sv.h_sc[s].repl;
-      if (werr && sv.h_sc[s].status == MSTOPO_OK && sv.h_sc[s].active) sv.h_sc[s].status = werr;
+      rr_last[s] = sv.h_sc[s].rr;
+      if (sv.h_sc[s].ff == 0.0) {
+        h->err = "zero load vector";
+        return MSTOPO_INVALID_ARG;
+      }
+      if (!sv.h_sc[s].active) done[s] = 1;
     }
   }
   // Without graphs (or with per-kernel profiling) the host decides after every iteration,
@@ -694,19 +722,48 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
     }
     if (total_iters > h->p.max_iter + chunk) break;
   }
-  CK(cudaEventRecord(ev1, h->s));
+  CK(cudaEventRecord(sv.ev1, h->s));
   // outputs
   CK(cudaMemcpyAsync(u, sv.x, (size_t)nsys * n * 8, cudaMemcpyDeviceToDevice, h->s));
   // compliance f^T u
   CK(launch_dot_partials(sv.f, sv.x, n, nsys, n, sv.partials, h->s));
   CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
-  double comp[MSTOPO_MAX_SYS];
-  CK(cudaMemcpyAsync(comp, vtmp, nsys * 8, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(sv.h_comp, vtmp, nsys * 8, cudaMemcpyDeviceToHost, h->s));
+  sv.run_sys0 = sys0;
+  sv.run_nsys = nsys;
+  sv.run_looped = looped ? 1 : 0;
+  for (int s = 0; s < nsys; ++s) sv.run_repl[s] = repl[s];
+  sv.run_pending = 1;
+  return MSTOPO_OK;
+}
+
+mstopo_status fcg_finish(mstopo_handle* h, mstopo_solve_info* infos) {
+  Solver& sv = h->sv;
+  if (!sv.run_pending) {
+    h->err = "no solve in flight";
+    return MSTOPO_INVALID_ARG;
+  }
+  sv.run_pending = 0;
   CK(cudaStreamSynchronize(h->s));
+  const int nsys = sv.run_nsys;
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, ev0, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
+  cudaEventElapsedTime(&ms, sv.ev0, sv.ev1);
+  const int* h_ints = reinterpret_cast<const int*>(sv.h_comp + MSTOPO_MAX_SYS);
+  if (sv.run_looped) {
+    const FcgGraph& gr = h->fcg_graph;
+    // passes of the loop body and of the true-residual body, and the loop's start kernel
+    g_launch_count.fetch_add((long long)h_ints[0] * gr.loop_launches + (long long)h_ints[1] * gr.true_launches + 1);
+    const int werr = h_ints[2];
+    for (int s = 0; s < nsys; ++s) {
+      FcgScalars& c = sv.h_sc[s];
+      sv.run_repl[s] = c.repl;
+      if (werr && c.status == MSTOPO_OK && c.active) c.status = werr;
+      if (c.ff == 0.0) {
+        h->err = "zero load vector";
+        return MSTOPO_INVALID_ARG;
+      }
+    }
+  }
   mstopo_status worst = MSTOPO_OK;
   for (int s = 0; s < nsys; ++s) {
     const FcgScalars& c = sv.h_sc[s];
@@ -714,12 +771,19 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
     if (infos) {
       infos[s].status = c.status;
       infos[s].iterations = c.iters;
-      infos[s].replacements = repl[s];
+      infos[s].replacements = sv.run_repl[s];
       infos[s].rel_residual = std::sqrt(c.rr / c.ff);
-      infos[s].compliance = comp[s];
+      infos[s].compliance = sv.h_comp[s];
       infos[s].ms = ms;
     }
   }
   if (worst != MSTOPO_OK) h->err = "flexible CG did not converge (see per-system status)";
   return worst;
+}
+
+mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
+                        const double* u0, mstopo_solve_info* infos) {
+  mstopo_status st = fcg_start(h, sys0, nsys, f, u, u0);
+  if (st != MSTOPO_OK) return st;
+  return fcg_finish(h, infos);
 }
