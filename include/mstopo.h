@@ -72,7 +72,7 @@ typedef enum {
 } mstopo_preconditioner;
 
 typedef enum {
-  MSTOPO_PATCH_AUTO = 0,           /* by problem size: the tensor cores from 32 patch solves per SM */
+  MSTOPO_PATCH_AUTO = 0,           /* by problem size: the tensor cores from 128 patch solves per SM */
   MSTOPO_PATCH_CUDA_CORES = 1,     /* FP32 and FP64 patch solves on the CUDA cores              */
   MSTOPO_PATCH_TENSOR_CORES = 2    /* MIXED: FP32 patch solves on the tensor cores (TF32 pairs) */
 } mstopo_patch_kernel;

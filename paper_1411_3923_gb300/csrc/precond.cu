@@ -1256,9 +1256,11 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     // the CUDA-core patch solves stream the packed blocks (FP64 always, FP32 unless the tensor
     // cores take the FP32 patch solves)
     // The tensor-core kernel's line has a fixed MMA chain (68 tcgen05.mma whatever the number
-    // of columns): it pays off with full 16-column groups and two CTAs per SM; on small
-    // problems (a few patches per SM) the CUDA-core kernel's shorter line wins.
-    pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 32LL * sms);
+    // of columns) and streams its own factor format; it pays off only with many full
+    // 16-column groups per SM.  Measured (MIXED solves, all realisations): 2048x1024, 42
+    // patches per SM: CUDA cores 220 ms, tensor cores 275 ms; 3200x4096, 257 per SM: CUDA
+    // cores 603 ms, tensor cores 557 ms.  The switch sits between the two.
+    pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 128LL * sms);
     const size_t tl = (size_t)TP * patch_tri_system_elems(nbP, NP);
     CKB(cudaMalloc(&pc.d_tri64, tl * 8));
     if (!pc.patch_tc) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
