@@ -77,6 +77,15 @@ typedef enum {
   MSTOPO_PATCH_TENSOR_CORES = 2    /* MIXED: FP32 patch solves on the tensor cores (TF32 pairs) */
 } mstopo_patch_kernel;
 
+typedef enum {
+  MSTOPO_KRYLOV_FCG = 0,           /* flexible conjugate gradients FCG(1) with reliable updates */
+  MSTOPO_KRYLOV_GMRES = 1          /* restarted GMRES(m), right preconditioned and flexible (the
+                                      preconditioned directions z_j are kept): the outer method
+                                      the paper uses with its multiplicative preconditioner
+                                      (Sec. 2.4.2); each restart starts from the true FP64
+                                      residual and the solve stops on it, as with FCG */
+} mstopo_krylov;
+
 /* mstopo_problem.exec_flags (bits; 0 = defaults) */
 #define MSTOPO_EXEC_NO_GRAPHS 1       /* run every flexible-CG iteration as direct launches      */
 #define MSTOPO_EXEC_NO_SIDE_STREAM 2  /* run the preconditioner's coarse chain on the main stream
@@ -118,6 +127,9 @@ typedef struct {
   int32_t preconditioner;    /* mstopo_preconditioner                                       */
   int32_t patch_kernel;      /* mstopo_patch_kernel: FP32 patch solves of the additive level */
   int32_t exec_flags;        /* MSTOPO_EXEC_* bits                                           */
+  int32_t krylov;            /* mstopo_krylov: the outer Krylov method                       */
+  int32_t gmres_restart;     /* GMRES(m) restart length m, 1..200 (0 = 50); GMRES keeps m + 1
+                                FP64 basis vectors and m FP64 preconditioned ones per handle */
 } mstopo_problem;
 
 typedef struct {

@@ -93,7 +93,9 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             (d->preconditioner == MSTOPO_PREC_ADDITIVE ||
              d->preconditioner == MSTOPO_PREC_MULTIPLICATIVE_SGS) &&
             d->patch_kernel >= MSTOPO_PATCH_AUTO && d->patch_kernel <= MSTOPO_PATCH_TENSOR_CORES &&
-            (d->exec_flags & ~(MSTOPO_EXEC_NO_GRAPHS | MSTOPO_EXEC_NO_SIDE_STREAM)) == 0;
+            (d->exec_flags & ~(MSTOPO_EXEC_NO_GRAPHS | MSTOPO_EXEC_NO_SIDE_STREAM)) == 0 &&
+            (d->krylov == MSTOPO_KRYLOV_FCG || d->krylov == MSTOPO_KRYLOV_GMRES) &&
+            d->gmres_restart >= 0 && d->gmres_restart <= 200;
   if (!ok) {
     h->err = "invalid problem description";
     return fail(MSTOPO_INVALID_ARG);
@@ -165,6 +167,7 @@ void mstopo_destroy(mstopo_handle* h) {
   else cudaDeviceSynchronize();
   precond_free(h->pc);
   solver_free(h->sv);
+  gmres_free(h->gm);
   prof_free(h->prof);
   if (h->fcg_graph.exec) cudaGraphExecDestroy(h->fcg_graph.exec);
   if (h->fcg_graph.loop) cudaGraphExecDestroy(h->fcg_graph.loop);

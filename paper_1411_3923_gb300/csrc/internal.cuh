@@ -204,6 +204,19 @@ struct Solver {
   int run_repl[MSTOPO_MAX_SYS] = {0};
 };
 
+// GMRES(m) workspace (gmres.cu), allocated at the first GMRES solve of a handle
+struct GmresWork {
+  int m = 0;
+  long long n = 0;
+  double* V = nullptr;              // [m + 1][n] orthonormal basis
+  double* Z = nullptr;              // [m][n] preconditioned directions
+  double* w = nullptr;              // [n]
+  double* small = nullptr;          // H, rotations, g, y, Gram-Schmidt columns, status
+  double* partials = nullptr;       // [m + 1][RED_BLOCKS]
+  double* h_st = nullptr;           // pinned [4]
+};
+void gmres_free(GmresWork& g);
+
 struct mstopo_handle {
   mstopo_problem p{};
   int device = 0;                   // CUDA device current at creation
@@ -228,6 +241,7 @@ struct mstopo_handle {
   // preconditioner, solver
   Precond pc;
   Solver sv;
+  GmresWork gm;
   int pc_ref = -1;
   int u_all_ready = 0;
   double* d_u_all = nullptr;        // [MAX_SYS][n_dof] last all-realisation solution
@@ -281,6 +295,9 @@ mstopo_status fcg_solve(mstopo_handle* h, int sys0, int nsys, const double* f, d
 mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, double* u,
                         const double* u0);
 mstopo_status fcg_finish(mstopo_handle* h, mstopo_solve_info* infos);
+// GMRES(m) of systems sys0 .. sys0 + nsys - 1 from the masked f and x0 in the solver's
+// vectors; fills the solver's host scalars (status, iters, rr, ff, repl = cycles) (gmres.cu)
+mstopo_status gmres_run(mstopo_handle* h, int sys0, int nsys);
 mstopo_status solver_alloc(mstopo_handle* h);
 void solver_free(Solver& sv);
 

@@ -456,6 +456,22 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
   for (int s = 0; s < nsys; ++s) sv.h_sc[s] = init;
   CK(cudaMemcpyAsync(sv.sc, sv.h_sc, nsys * sizeof(FcgScalars), cudaMemcpyHostToDevice, h->s));
   double* vtmp = sv.partials + (size_t)MSTOPO_MAX_SYS * 3 * RB;   // small scratch [nsys]
+  if (h->p.krylov == MSTOPO_KRYLOV_GMRES) {
+    // GMRES(m) fills the host scalars itself; the outputs below are the same
+    st = gmres_run(h, sys0, nsys);
+    if (st != MSTOPO_OK) return st;
+    CK(cudaEventRecord(sv.ev1, h->s));
+    CK(cudaMemcpyAsync(u, sv.x, (size_t)nsys * n * 8, cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_dot_partials(sv.f, sv.x, n, nsys, n, sv.partials, h->s));
+    CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
+    CK(cudaMemcpyAsync(sv.h_comp, vtmp, nsys * 8, cudaMemcpyDeviceToHost, h->s));
+    sv.run_sys0 = sys0;
+    sv.run_nsys = nsys;
+    sv.run_looped = 0;
+    for (int s = 0; s < nsys; ++s) sv.run_repl[s] = sv.h_sc[s].repl;
+    sv.run_pending = 1;
+    return MSTOPO_OK;
+  }
   CK(launch_dot_partials(sv.f, sv.f, n, nsys, n, sv.partials, h->s));
   CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
   note_launch(), k_set_rr<<<1, nsys, 0, h->s>>>(sv.sc, vtmp, 0, tol2);
@@ -764,6 +780,11 @@ mstopo_status fcg_finish(mstopo_handle* h, mstopo_solve_info* infos) {
       }
     }
   }
+  for (int s = 0; s < nsys; ++s)
+    if (sv.h_sc[s].status == MSTOPO_INVALID_ARG && sv.h_sc[s].ff == 0.0) {
+      h->err = "zero load vector";
+      return MSTOPO_INVALID_ARG;
+    }
   mstopo_status worst = MSTOPO_OK;
   for (int s = 0; s < nsys; ++s) {
     const FcgScalars& c = sv.h_sc[s];

@@ -36,7 +36,8 @@ class _Problem(C.Structure):
                 ("local_shift", C.c_double), ("stream", C.c_void_p),
                 ("coarse_solver", C.c_int32), ("reuse_preconditioner", C.c_int32),
                 ("rebuild_ratio", C.c_double), ("preconditioner", C.c_int32),
-                ("patch_kernel", C.c_int32), ("exec_flags", C.c_int32)]
+                ("patch_kernel", C.c_int32), ("exec_flags", C.c_int32),
+                ("krylov", C.c_int32), ("gmres_restart", C.c_int32)]
 
 
 class _BuildInfo(C.Structure):
@@ -58,6 +59,7 @@ COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
 PRECONDITIONERS = {"additive": 0, "sgs": 1}   # mstopo_preconditioner
 PATCH_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}   # mstopo_patch_kernel
 EXEC_NO_GRAPHS, EXEC_NO_SIDE_STREAM = 1, 2   # mstopo_problem.exec_flags bits
+KRYLOV = {"fcg": 0, "gmres": 1}   # mstopo_krylov
 
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
 
@@ -155,7 +157,8 @@ class Problem:
                  stream: Optional[int] = None, coarse_solver: str = "auto",
                  reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0,
                  preconditioner: str = "additive", patch_kernel: str = "auto",
-                 graphs: bool = True, side_stream: bool = True):
+                 graphs: bool = True, side_stream: bool = True, krylov: str = "fcg",
+                 gmres_restart: int = 0):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
@@ -165,7 +168,8 @@ class Problem:
                      local_shift, stream, COARSE_SOLVERS[coarse_solver],
                      1 if reuse_preconditioner else 0, rebuild_ratio,
                      PRECONDITIONERS[preconditioner], PATCH_KERNELS[patch_kernel],
-                     (0 if graphs else EXEC_NO_GRAPHS) | (0 if side_stream else EXEC_NO_SIDE_STREAM))
+                     (0 if graphs else EXEC_NO_GRAPHS) | (0 if side_stream else EXEC_NO_SIDE_STREAM),
+                     KRYLOV[krylov], gmres_restart)
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))
         if st != 0:

@@ -615,3 +615,44 @@ def test_device_side_loop_equals_host_driven_loop(precision):
         assert all(i["status"] == 0 and i["rel_residual"] <= 1e-10 for i in infos)
     assert torch.equal(out[True][0], out[False][0])
     assert out[True][1] == out[False][1] and out[True][2] == out[False][2]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("etas", [(0.5,), (0.3, 0.5, 0.7)])
+def test_gmres_with_multiplicative_sgs_matches_oracle(precision, etas):
+    """GMRES(m), the paper's outer method for its multiplicative preconditioner (Sec. 2.4.2),
+    restarted every 20 steps: every realisation converges to the sparse-LU solution, and the
+    iteration count is the oracle's GMRES on the same operator (its SGS in the GPU's colour
+    order and the same spectral coarse space)."""
+    m = _gpu()
+    wl = workloads.small(96, 48, seed=33, kind="voids", H=8, n_eig=6, etas=etas, rmin=2.0,
+                         beta=8.0)
+    prob = make_problem(m, wl, precision, tol=1e-10, preconditioner="sgs", krylov="gmres",
+                        gmres_restart=20)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
+    u, infos = prob.solve(cuda(wl.force), -1)
+    u2, _ = prob.solve(cuda(wl.force), -1)
+    assert torch.equal(u, u2)   # deterministic reductions
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    grid, K0, oprob, chain = pipeline.build(wl)
+    E = chain.forward(wl.rho)["E"]
+    for k, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        Kf = oprob.free_matrix(ref["E"][k])
+        ug = grid.nodal_from_neutral(u[k].cpu().numpy())[oprob.free]
+        ur = grid.nodal_from_neutral(ref["u"][k])[oprob.free]
+        assert_energy(Kf, ur, ug)
+        assert inf["compliance"] == pytest.approx(ref["c"][k], rel=1e-10)
+    # the oracle's GMRES with the preconditioner built on each realisation's moduli (the
+    # coarse basis from the dilated realisation, as the library builds it)
+    k0 = 0
+    K = oprob.free_matrix(E[k0])
+    tl = msfem.TwoLevel(oprob, E[k0], wl.H, wl.n_eig, with_patches=False)
+    Mref = smoother.MultiplicativeTwoLevel(K, smoother.SymmetricGaussSeidel(oprob, K, "colour"),
+                                           tl.coarse)
+    f = grid.nodal_from_neutral(wl.force)[oprob.free]
+    _, it_ref, rel_ref = smoother.gmres(K, f, Mref.apply, tol=1e-10, restart=20, maxit=2000)
+    print("GPU", [i["iterations"] for i in infos], "oracle", it_ref, rel_ref)
+    assert rel_ref <= 1e-10
+    assert abs(infos[k0]["iterations"] - it_ref) <= max(2, 0.05 * it_ref)

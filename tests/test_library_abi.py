@@ -106,3 +106,19 @@ def test_unknown_patch_kernel_or_exec_flag_is_rejected(patch_kernel, exec_flags)
     h = ctypes.c_void_p()
     assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert h.value is None
+
+
+@pytest.mark.parametrize("krylov,restart", [(2, 0), (-1, 0), (1, -1), (1, 201)])
+def test_unknown_krylov_method_or_restart_is_rejected(krylov, restart):
+    """The outer method and the GMRES restart length are validated before any GPU work."""
+    import ctypes
+    import numpy as np
+    import paper_1411_3923_gb300 as m
+    from paper_1411_3923_gb300 import mstopo
+    lib = m.load()
+    fixed = np.zeros(2 * 9 * 9, np.uint8)
+    d = mstopo._Problem(8, 8, 0.3, 1.0, 1e-9, 3.0, fixed.ctypes.data, 4, 4, 0.0, 1, 1e-8, 100,
+                        0.0, None, 0, 0, 0.0, 0, 0, 0, krylov, restart)
+    h = ctypes.c_void_p()
+    assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert h.value is None
