@@ -293,6 +293,51 @@ mstopo_status mstopo_apply_K_f32_noalloc(const double* u, double* y, const float
                                         const uint8_t* fixed, int32_t nelx, int32_t nely,
                                         double nu, void* stream);
 
+/* ---- PDE (Helmholtz) density filter with collapsed degrees of freedom (Sec. 4.3, 4.5) --- */
+
+/* The filter of designs made of several microstructure blocks: on the filter mesh (unit Q4
+ * elements, cells of nx x ny[c] elements stacked along y, each cell with its own nodes)
+ *   -r^2 lap(phi) + phi = rho,  r = rmin / (2 sqrt(3)),  natural boundary conditions,
+ *   rho_tilde_e = mean of phi over the element's four nodes,
+ * where identified nodes share one unknown (periodicity and connectivity).  The operator
+ * rho -> rho_tilde is symmetric: the sensitivity chain applies it unchanged.  Solved by
+ * Jacobi-preconditioned CG in FP64 on the collapsed unknowns, matrix-free. */
+typedef enum {
+  MSTOPO_PDE_PLAIN = 0,           /* one cell, no identification (Neumann on the whole boundary) */
+  MSTOPO_PDE_PERIODIC_CELL = 1,   /* one cell, left = right and bottom = top edges (a torus)     */
+  MSTOPO_PDE_STACKED_BLOCKS = 2   /* n_cells cells of width nx stacked along y: each cell's left
+                                     and right edges identified, and the bottom and top edges of
+                                     all cells one set (periodic within each block, connected
+                                     across the interfaces) */
+} mstopo_pde_domain;
+
+typedef struct {
+  int32_t domain;            /* mstopo_pde_domain                                           */
+  int32_t nx;                /* elements along x of every cell, >= 1                        */
+  int32_t n_cells;           /* cells (1 unless MSTOPO_PDE_STACKED_BLOCKS)                  */
+  const int32_t* ny;         /* HOST [n_cells]: elements along y of each cell, >= 1         */
+  double rmin;               /* filter radius in elements, > 0                               */
+  double tol;                /* CG stop: ||b - K phi|| <= tol ||b|| (0 = 1e-12)             */
+  int32_t max_iter;          /* CG iteration cap (0 = 1000)                                  */
+  void* stream;              /* cudaStream_t for all work of the filter, NULL = default      */
+} mstopo_pde_desc;
+
+typedef struct mstopo_pde_filter mstopo_pde_filter;
+
+/* Builds the collapse map and the CG workspace (device memory owned by the filter).
+ * Errors: INVALID_ARG (bad description; the message is mstopo_pde_filter_last_error(NULL)),
+ * OUT_OF_MEMORY, CUDA_ERROR. */
+mstopo_status mstopo_pde_filter_create(const mstopo_pde_desc* d, mstopo_pde_filter** out);
+/* rho_tilde = filter(rho).  rho, rho_tilde: DEVICE [n_elements] FP64, elements cell by cell,
+ * row by row (x fastest).  iterations, rel_residual: HOST, may be NULL.  Synchronises the
+ * filter's stream.  Errors: INVALID_ARG (null pointer), MAX_ITER, NONFINITE, CUDA_ERROR. */
+mstopo_status mstopo_pde_filter_apply(mstopo_pde_filter* f, const double* rho, double* rho_tilde,
+                                      int32_t* iterations, double* rel_residual);
+int64_t mstopo_pde_filter_num_elements(const mstopo_pde_filter* f);
+int64_t mstopo_pde_filter_num_unknowns(const mstopo_pde_filter* f);   /* after collapsing */
+const char* mstopo_pde_filter_last_error(const mstopo_pde_filter* f);
+void mstopo_pde_filter_destroy(mstopo_pde_filter* f);
+
 /* ---- measurement (not part of the paper's method) ----------------------------------- */
 
 typedef struct {
@@ -303,8 +348,8 @@ typedef struct {
   int32_t base_iterations;     /* iterations of the first solve after the last build, or -1  */
   int32_t rebuild_pending;     /* 1: the next all-realisation solve rebuilds first            */
   int64_t device_loop_solves;  /* solves of this handle whose iteration loop ran as one CUDA
-                                  graph with device-side convergence tests (the others ran
-                                  host-driven chunks: graphs off or per-kernel profiling on) */
+                                  graph with device-side convergence tests (the others ran a
+                                  host-driven loop: graphs off or per-kernel profiling on) */
 } mstopo_stats;
 
 /* Turn per-kernel event timing on (1) or off (0) for this handle; resets its counters.

@@ -64,6 +64,15 @@ KRYLOV = {"fcg": 0, "gmres": 1}   # mstopo_krylov
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
 
 
+class _PdeDesc(C.Structure):
+    _fields_ = [("domain", C.c_int32), ("nx", C.c_int32), ("n_cells", C.c_int32),
+                ("ny", C.c_void_p), ("rmin", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("stream", C.c_void_p)]
+
+
+PDE_DOMAINS = {"plain": 0, "periodic_cell": 1, "stacked_blocks": 2}   # mstopo_pde_domain
+
+
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("replacements", C.c_int32),
                 ("rel_residual", C.c_double), ("compliance", C.c_double), ("ms", C.c_float)]
@@ -77,7 +86,10 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_compliance_and_sensitivity", "mstopo_apply_K", "mstopo_apply_K_f32",
            "mstopo_apply_precond", "mstopo_get_eigenpairs", "mstopo_set_profiling",
            "mstopo_get_stats", "mstopo_apply_K_f32_noalloc", "mstopo_batch_build_preconditioner",
-           "mstopo_batch_solve", "mstopo_apply_K_f32_ex", "mstopo_inject"]
+           "mstopo_batch_solve", "mstopo_apply_K_f32_ex", "mstopo_inject",
+           "mstopo_pde_filter_create", "mstopo_pde_filter_apply", "mstopo_pde_filter_num_elements",
+           "mstopo_pde_filter_num_unknowns", "mstopo_pde_filter_last_error",
+           "mstopo_pde_filter_destroy"]
 
 
 def load(path: str = LIB_PATH):
@@ -113,6 +125,12 @@ def load(path: str = LIB_PATH):
         "mstopo_apply_K_f32_ex": ([vp, i32, vp, vp, i32], i32),
         "mstopo_inject": ([vp, i32], i32),
         "mstopo_apply_K_f32_noalloc": ([vp, vp, vp, vp, i32, i32, dbl, vp], i32),
+        "mstopo_pde_filter_create": ([C.POINTER(_PdeDesc), C.POINTER(vp)], i32),
+        "mstopo_pde_filter_apply": ([vp, vp, vp, C.POINTER(i32), C.POINTER(dbl)], i32),
+        "mstopo_pde_filter_num_elements": ([vp], i64),
+        "mstopo_pde_filter_num_unknowns": ([vp], i64),
+        "mstopo_pde_filter_last_error": ([vp], C.c_char_p),
+        "mstopo_pde_filter_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -366,3 +384,50 @@ def batch_solve(problems, fs):
     if st != 0:
         raise MstopoError(st, f"batch solve: {out}")
     return us, out
+
+
+class PDEFilter:
+    """The PDE (Helmholtz) density filter with collapsed degrees of freedom (Sec. 4.3, 4.5) of
+    include/mstopo.h: ``domain`` "plain", "periodic_cell" or "stacked_blocks" (cells of width
+    nx and heights ny stacked along y).  ``apply(rho)`` takes and returns a CUDA FP64 tensor of
+    the design elements (cell by cell, row by row); the operator is symmetric."""
+
+    def __init__(self, domain: str, nx: int, ny, rmin: float, *, tol: float = 1e-12,
+                 max_iter: int = 0, stream: Optional[int] = None):
+        lib = load()
+        heights = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
+        self._ny = np.ascontiguousarray(heights, dtype=np.int32)
+        d = _PdeDesc(PDE_DOMAINS[domain], nx, len(heights), self._ny.ctypes.data, rmin, tol,
+                     max_iter, stream)
+        h = C.c_void_p()
+        st = lib.mstopo_pde_filter_create(C.byref(d), C.byref(h))
+        if st != 0:
+            raise MstopoError(st, lib.mstopo_pde_filter_last_error(None).decode())
+        self._h = h
+        self.n_el = int(lib.mstopo_pde_filter_num_elements(h))
+        self.n_unknowns = int(lib.mstopo_pde_filter_num_unknowns(h))
+        self.iterations, self.rel_residual = 0, 0.0
+
+    def apply(self, rho: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        rho = _dev(rho)
+        assert rho.numel() == self.n_el
+        if out is None:
+            out = torch.empty_like(rho)
+        it, res = C.c_int32(), C.c_double()
+        st = _lib.mstopo_pde_filter_apply(self._h, rho.data_ptr(), out.data_ptr(), C.byref(it),
+                                          C.byref(res))
+        if st != 0:
+            raise MstopoError(st, _lib.mstopo_pde_filter_last_error(self._h).decode())
+        self.iterations, self.rel_residual = it.value, res.value
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mstopo_pde_filter_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

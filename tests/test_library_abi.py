@@ -49,7 +49,8 @@ def test_invalid_problem_is_rejected_without_gpu_work():
 @pytest.mark.parametrize("c_name,py_name", [("mstopo_problem", "_Problem"),
                                              ("mstopo_build_info", "_BuildInfo"),
                                              ("mstopo_solve_info", "_SolveInfo"),
-                                             ("mstopo_stats", "_Stats")])
+                                             ("mstopo_stats", "_Stats"),
+                                             ("mstopo_pde_desc", "_PdeDesc")])
 def test_ctypes_structs_match_the_header_layout(tmp_path, c_name, py_name):
     """Every public struct of include/mstopo.h has the same size and field offsets in the
     binding's ctypes mirror: a C program compiled against the header prints them."""
@@ -122,3 +123,20 @@ def test_unknown_krylov_method_or_restart_is_rejected(krylov, restart):
     h = ctypes.c_void_p()
     assert lib.mstopo_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert h.value is None
+
+
+@pytest.mark.parametrize("domain,nx,ny,rmin", [(3, 8, [8], 2.0), (1, 8, [8, 8], 2.0), (0, 0, [8], 2.0),
+                                              (2, 8, [8, 0], 2.0), (0, 8, [8], 0.0)])
+def test_invalid_pde_filter_is_rejected_without_gpu_work(domain, nx, ny, rmin):
+    """mstopo_pde_filter_create validates the description before any device call."""
+    import ctypes
+    import numpy as np
+    import paper_1411_3923_gb300 as m
+    from paper_1411_3923_gb300 import mstopo
+    lib = m.load()
+    h = np.ascontiguousarray(ny, dtype=np.int32)
+    d = mstopo._PdeDesc(domain, nx, len(ny), h.ctypes.data, rmin, 0.0, 0, None)
+    f = ctypes.c_void_p()
+    assert lib.mstopo_pde_filter_create(ctypes.byref(d), ctypes.byref(f)) == 1
+    assert f.value is None
+    assert b"invalid" in lib.mstopo_pde_filter_last_error(None)
