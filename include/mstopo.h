@@ -338,6 +338,63 @@ int64_t mstopo_pde_filter_num_unknowns(const mstopo_pde_filter* f);   /* after c
 const char* mstopo_pde_filter_last_error(const mstopo_pde_filter* f);
 void mstopo_pde_filter_destroy(mstopo_pde_filter* f);
 
+/* ---- the design loop (Sec. 4.4, 4.5) ------------------------------------------------- */
+
+/* The expected-volume constraint of the robust problem (Sec. 4.4) at the current design:
+ * g = E[vol(rho_bar)] / volfrac - 1 (the mean of rho_bar over the realisations and the
+ * design elements; a periodic cell stands for each of its tiles equally) and its gradient
+ * with respect to the design, through the projection and the filter transpose.
+ * g: HOST, may be NULL; dgdrho: DEVICE [n_design], may be NULL.  Synchronises the stream.
+ * Errors: NOT_READY (no design), INVALID_ARG (volfrac outside (0, 1]), CUDA_ERROR. */
+mstopo_status mstopo_volume(mstopo_handle* h, double volfrac, double* g, double* dgdrho);
+
+/* The method of moving asymptotes (Svanberg 1987) for one inequality constraint
+ * g(x) <= 0 on xmin <= x <= xmax: asymptotes at x -/+ s0 (xmax - xmin) in the first two
+ * steps, then moved by 0.7 / 1.2 where x oscillates / moves monotonically, and the convex
+ * separable subproblem solved through its one-dimensional dual.  The object keeps the
+ * asymptotes and the last two iterates (device memory it owns). */
+typedef struct mstopo_mma mstopo_mma;
+mstopo_status mstopo_mma_create(int64_t n, double xmin, double xmax, double s0, void* stream,
+                                mstopo_mma** out);
+/* One step from x with the objective f0, its gradient df0, the constraint value g and its
+ * gradient dg: xnew.  x, df0, dg, xnew: DEVICE [n] FP64 (xnew must not alias x).  lam: HOST,
+ * the constraint's multiplier, may be NULL.  Synchronises the stream.  Errors: INVALID_ARG,
+ * NONFINITE (f0 or g), CUDA_ERROR. */
+mstopo_status mstopo_mma_step(mstopo_mma* m, const double* x, double f0, const double* df0,
+                              double g, const double* dg, double* xnew, double* lam);
+const char* mstopo_mma_last_error(const mstopo_mma* m);
+void mstopo_mma_destroy(mstopo_mma* m);
+
+typedef struct {
+  double penal;              /* SIMP exponent of this stage, >= 1                            */
+  double beta;               /* projection sharpness of this stage, > 0                      */
+  int32_t max_iter;          /* design iterations of this stage, >= 1                        */
+} mstopo_opt_stage;
+
+typedef struct {
+  int32_t stage, iteration;
+  double penal, beta;
+  double f;                  /* robust objective E[c] + kappa std(c)                         */
+  double g;                  /* volume constraint value                                     */
+  double c[4];               /* compliance of every realisation                             */
+  int32_t solve_iterations;  /* the largest Krylov iteration count of the state solves      */
+} mstopo_opt_record;
+
+/* Robust compliance minimisation (Sec. 4.4) with the continuation schedule of Sec. 4.5.
+ * Every stage starts new asymptotes (s0 = 0.5 / (1 + beta)); each iteration sets the design
+ * (the filter radius, thresholds and cell of the last mstopo_set_design, the stage's beta and
+ * penal), builds the preconditioner unless it is reused, solves all realisations for the load
+ * f (DEVICE [n_dof]), forms the objective, its gradient and the volume constraint, and takes
+ * one MMA step; a stage ends after max_iter iterations or when the objective changes by at
+ * most rel_change (relative) between two iterations.  rho: DEVICE [n_design], the start design
+ * in, the final one out.  records: HOST [capacity] history (one per iteration), may be NULL
+ * with capacity 0; n_records: HOST, the iterations made.  The handle keeps the last stage's
+ * penal.  Errors: INVALID_ARG, NOT_READY (no design set before), and those of the steps. */
+mstopo_status mstopo_optimise(mstopo_handle* h, double* rho, const double* f,
+                              const mstopo_opt_stage* stages, int32_t n_stages, double volfrac,
+                              double kappa, double rel_change, mstopo_opt_record* records,
+                              int32_t capacity, int32_t* n_records);
+
 /* ---- measurement (not part of the paper's method) ----------------------------------- */
 
 typedef struct {

@@ -73,6 +73,16 @@ class _PdeDesc(C.Structure):
 PDE_DOMAINS = {"plain": 0, "periodic_cell": 1, "stacked_blocks": 2}   # mstopo_pde_domain
 
 
+class _OptStage(C.Structure):
+    _fields_ = [("penal", C.c_double), ("beta", C.c_double), ("max_iter", C.c_int32)]
+
+
+class _OptRecord(C.Structure):
+    _fields_ = [("stage", C.c_int32), ("iteration", C.c_int32), ("penal", C.c_double),
+                ("beta", C.c_double), ("f", C.c_double), ("g", C.c_double),
+                ("c", C.c_double * 4), ("solve_iterations", C.c_int32)]
+
+
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("replacements", C.c_int32),
                 ("rel_residual", C.c_double), ("compliance", C.c_double), ("ms", C.c_float)]
@@ -89,7 +99,8 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_batch_solve", "mstopo_apply_K_f32_ex", "mstopo_inject",
            "mstopo_pde_filter_create", "mstopo_pde_filter_apply", "mstopo_pde_filter_num_elements",
            "mstopo_pde_filter_num_unknowns", "mstopo_pde_filter_last_error",
-           "mstopo_pde_filter_destroy"]
+           "mstopo_pde_filter_destroy", "mstopo_volume", "mstopo_mma_create", "mstopo_mma_step",
+           "mstopo_mma_last_error", "mstopo_mma_destroy", "mstopo_optimise"]
 
 
 def load(path: str = LIB_PATH):
@@ -131,6 +142,13 @@ def load(path: str = LIB_PATH):
         "mstopo_pde_filter_num_unknowns": ([vp], i64),
         "mstopo_pde_filter_last_error": ([vp], C.c_char_p),
         "mstopo_pde_filter_destroy": ([vp], None),
+        "mstopo_volume": ([vp, dbl, C.POINTER(dbl), vp], i32),
+        "mstopo_mma_create": ([i64, dbl, dbl, dbl, vp, C.POINTER(vp)], i32),
+        "mstopo_mma_step": ([vp, vp, dbl, vp, dbl, vp, vp, C.POINTER(dbl)], i32),
+        "mstopo_mma_last_error": ([vp], C.c_char_p),
+        "mstopo_mma_destroy": ([vp], None),
+        "mstopo_optimise": ([vp, vp, vp, C.POINTER(_OptStage), i32, dbl, dbl, dbl,
+                             C.POINTER(_OptRecord), i32, C.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -424,6 +442,75 @@ class PDEFilter:
     def close(self):
         if getattr(self, "_h", None):
             _lib.mstopo_pde_filter_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+
+def _problem_volume(self, volfrac: float, want_grad: bool = True):
+    """The expected-volume constraint g = E[vol(rho_bar)] / volfrac - 1 at the current design
+    and (want_grad) its gradient with respect to the design (Sec. 4.4)."""
+    g = C.c_double()
+    dg = torch.empty(self.n_design, dtype=torch.float64, device="cuda") if want_grad else None
+    self._check(_lib.mstopo_volume(self._h, volfrac, C.byref(g), _ptr(dg)))
+    return (g.value, dg) if want_grad else g.value
+
+
+def _problem_optimise(self, rho: torch.Tensor, f: torch.Tensor, stages, volfrac: float,
+                      kappa: float = 1.0, rel_change: float = 1e-3, capacity: int = 10000):
+    """Robust compliance minimisation with continuation (Sec. 4.4, 4.5) on the device:
+    stages = [(penal, beta, max_iter), ...].  Needs an earlier set_design (its rmin, etas and
+    cell are kept).  Returns the final design and the history (one dict per iteration)."""
+    x = _dev(rho).clone()
+    fl = _dev(f)
+    st = (_OptStage * len(stages))(*[_OptStage(p, b, it) for p, b, it in stages])
+    rec = (_OptRecord * capacity)()
+    n = C.c_int32()
+    self._check(_lib.mstopo_optimise(self._h, x.data_ptr(), fl.data_ptr(), st, len(stages),
+                                     volfrac, kappa, rel_change, rec, capacity, C.byref(n)))
+    hist = [{"stage": r.stage, "iteration": r.iteration, "penal": r.penal, "beta": r.beta,
+             "f": r.f, "g": r.g, "c": list(r.c)[:self.n_eta],
+             "solve_iterations": r.solve_iterations} for r in rec[:min(n.value, capacity)]]
+    return x, hist
+
+
+Problem.volume = _problem_volume
+Problem.optimise = _problem_optimise
+
+
+class MMA:
+    """The method of moving asymptotes for one constraint (include/mstopo.h): step(x, f0, df0,
+    g, dg) with CUDA FP64 tensors of n design variables returns the next design."""
+
+    def __init__(self, n: int, xmin: float = 0.0, xmax: float = 1.0, s0: float = 0.5,
+                 stream: Optional[int] = None):
+        lib = load()
+        h = C.c_void_p()
+        st = lib.mstopo_mma_create(n, xmin, xmax, s0, stream, C.byref(h))
+        if st != 0:
+            raise MstopoError(st, lib.mstopo_mma_last_error(None).decode())
+        self._h, self.n, self.lam = h, n, 0.0
+
+    def step(self, x, f0: float, df0, g: float, dg) -> torch.Tensor:
+        x, df0, dg = _dev(x), _dev(df0), _dev(dg)
+        assert x.numel() == df0.numel() == dg.numel() == self.n
+        out = torch.empty_like(x)
+        lam = C.c_double()
+        st = _lib.mstopo_mma_step(self._h, x.data_ptr(), float(f0), df0.data_ptr(), float(g),
+                                  dg.data_ptr(), out.data_ptr(), C.byref(lam))
+        if st != 0:
+            raise MstopoError(st, _lib.mstopo_mma_last_error(self._h).decode())
+        self.lam = lam.value
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mstopo_mma_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -50,7 +50,9 @@ def test_invalid_problem_is_rejected_without_gpu_work():
                                              ("mstopo_build_info", "_BuildInfo"),
                                              ("mstopo_solve_info", "_SolveInfo"),
                                              ("mstopo_stats", "_Stats"),
-                                             ("mstopo_pde_desc", "_PdeDesc")])
+                                             ("mstopo_pde_desc", "_PdeDesc"),
+                                             ("mstopo_opt_stage", "_OptStage"),
+                                             ("mstopo_opt_record", "_OptRecord")])
 def test_ctypes_structs_match_the_header_layout(tmp_path, c_name, py_name):
     """Every public struct of include/mstopo.h has the same size and field offsets in the
     binding's ctypes mirror: a C program compiled against the header prints them."""
