@@ -395,6 +395,15 @@ mstopo_status mstopo_optimise(mstopo_handle* h, double* rho, const double* f,
                               double kappa, double rel_change, mstopo_opt_record* records,
                               int32_t capacity, int32_t* n_records);
 
+/* Robust verification (Sec. 4.4): the compliance of one design under n thresholds (for
+ * example uniformly spaced in [0.3, 0.7]), each an independent realisation.  The thresholds
+ * run in batches of up to 4 realisations (one set_design, build and solve each) with the
+ * filter radius, beta and cell of the last mstopo_set_design.  rho: DEVICE [n_design];
+ * f: DEVICE [n_dof]; etas: HOST [n], each in (0, 1); c: HOST [n].  The handle is left with
+ * the last batch as its design.  Errors: INVALID_ARG, NOT_READY, and those of the steps. */
+mstopo_status mstopo_robust_verification(mstopo_handle* h, const double* rho, const double* f,
+                                         const double* etas, int32_t n, double* c);
+
 /* ---- measurement (not part of the paper's method) ----------------------------------- */
 
 typedef struct {

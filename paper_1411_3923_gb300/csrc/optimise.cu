@@ -393,4 +393,33 @@ mstopo_status mstopo_optimise(mstopo_handle* H, double* rho, const double* f,
   return st;
 }
 
+mstopo_status mstopo_robust_verification(mstopo_handle* H, const double* rho, const double* f,
+                                         const double* etas, int32_t n, double* c) {
+  if (!H) return MSTOPO_INVALID_ARG;
+  if (!rho || !f || !etas || !c || n < 1) {
+    H->err = "invalid verification arguments";
+    return MSTOPO_INVALID_ARG;
+  }
+  if (H->n_design < 1) {
+    H->err = "set a design first (its filter radius, beta and cell are kept)";
+    return MSTOPO_NOT_READY;
+  }
+  const long long nd = H->n_design;
+  const double rmin = H->rmin, beta = H->beta;
+  const int cx = H->periodic ? H->dx : 0, cy = H->periodic ? H->dy : 0;
+  double* u = nullptr;
+  OCK(cudaMalloc(&u, (size_t)MSTOPO_MAX_SYS * H->n_dof * 8));
+  mstopo_status st = MSTOPO_OK;
+  for (int b = 0; b < n && st == MSTOPO_OK; b += MSTOPO_MAX_SYS) {
+    const int m = std::min(MSTOPO_MAX_SYS, n - b);
+    // each batch of thresholds is one set of realisations: its own coarse basis and factors
+    st = mstopo_set_design(H, rho, nd, rmin, beta, etas + b, m, cx, cy);
+    if (st == MSTOPO_OK && !H->pc.built) st = mstopo_build_preconditioner(H, -1, nullptr);
+    if (st == MSTOPO_OK) st = mstopo_solve(H, -1, f, u, nullptr, nullptr);
+    if (st == MSTOPO_OK) st = mstopo_compliance_and_sensitivity(H, 0.0, c + b, nullptr, nullptr);
+  }
+  cudaFree(u);
+  return st;
+}
+
 }  // extern "C"

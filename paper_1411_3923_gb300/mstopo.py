@@ -100,7 +100,8 @@ SYMBOLS = ["mstopo_create", "mstopo_destroy", "mstopo_last_error", "mstopo_num_d
            "mstopo_pde_filter_create", "mstopo_pde_filter_apply", "mstopo_pde_filter_num_elements",
            "mstopo_pde_filter_num_unknowns", "mstopo_pde_filter_last_error",
            "mstopo_pde_filter_destroy", "mstopo_volume", "mstopo_mma_create", "mstopo_mma_step",
-           "mstopo_mma_last_error", "mstopo_mma_destroy", "mstopo_optimise"]
+           "mstopo_mma_last_error", "mstopo_mma_destroy", "mstopo_optimise",
+           "mstopo_robust_verification"]
 
 
 def load(path: str = LIB_PATH):
@@ -149,6 +150,7 @@ def load(path: str = LIB_PATH):
         "mstopo_mma_destroy": ([vp], None),
         "mstopo_optimise": ([vp, vp, vp, C.POINTER(_OptStage), i32, dbl, dbl, dbl,
                              C.POINTER(_OptRecord), i32, C.POINTER(i32)], i32),
+        "mstopo_robust_verification": ([vp, vp, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -479,7 +481,18 @@ def _problem_optimise(self, rho: torch.Tensor, f: torch.Tensor, stages, volfrac:
     return x, hist
 
 
+def _problem_robust_verification(self, rho: torch.Tensor, f: torch.Tensor, etas) -> np.ndarray:
+    """Compliance of the design rho under every threshold in etas (Sec. 4.4)."""
+    e = np.ascontiguousarray(etas, dtype=np.float64)
+    c = np.zeros(e.size)
+    self._check(_lib.mstopo_robust_verification(self._h, _dev(rho).data_ptr(), _dev(f).data_ptr(),
+                                                e.ctypes.data, e.size, c.ctypes.data))
+    self.n_eta = min(e.size - ((e.size - 1) // 4) * 4, 4)
+    return c
+
+
 Problem.volume = _problem_volume
+Problem.robust_verification = _problem_robust_verification
 Problem.optimise = _problem_optimise
 
 

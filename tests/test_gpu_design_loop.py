@@ -89,3 +89,19 @@ def test_optimise_matches_oracle(etas):
         assert h["f"] == pytest.approx(r["f"], rel=1e-7)
         assert h["g"] == pytest.approx(r["g"], rel=1e-7, abs=1e-9)
     assert np.abs(rho.cpu().numpy().reshape(rho_ref.shape) - rho_ref).max() <= 1e-6
+
+
+def test_robust_verification_matches_oracle():
+    """Compliance of one design over seven thresholds spread on [0.3, 0.7] (Sec. 4.4): two
+    batches of realisations on the GPU against one direct solve per threshold."""
+    m = _gpu()
+    wl = workloads.small(48, 24, seed=43, kind="voids", H=8, n_eig=4, etas=(0.5,), rmin=2.0,
+                         beta=8.0)
+    etas = np.linspace(0.3, 0.7, 7)
+    prob = _problem(m, wl)
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    c = prob.robust_verification(cuda(wl.rho), cuda(wl.force), etas)
+    c_ref = optimise.robust_verification(wl, wl.rho, etas)
+    print(c, c_ref)
+    assert np.allclose(c, c_ref, rtol=1e-10, atol=0.0)
+    assert np.all(np.diff(c) > 0.0)    # thinner (eroded) designs are more compliant
