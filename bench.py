@@ -41,9 +41,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: 152 SMs x 2 FP64 FMA/clk (measured 1.19 TFLOP/s at ~1.95 GHz) x 2 x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one FP32 patch-solve launch on the 1024x512 workload, from an
-# ncu capture of `bench.py --only patch` (dram__bytes_read.sum + dram__bytes_write.sum of the
-# current kernel); None until the current kernel has been captured
-PATCH_TRAFFIC_BYTES = None
+# ncu capture of `bench.py --only patch --reps 3` (dram__bytes_read.sum 106.02 MB +
+# dram__bytes_write.sum 13.42 MB of k_patch_tri<float, 4, 1, 3, 1>, profiles/k_patch_tri_f32_mbb_c2.md);
+# set to None whenever the kernel changes until it is captured again
+PATCH_TRAFFIC_BYTES = 119_449_600
 
 
 def load_peaks():
