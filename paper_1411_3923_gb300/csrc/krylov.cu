@@ -48,6 +48,20 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;   // valid in thread 0
 }
 
+// The total of one system's RB block partials in every thread of the block: the same loop and
+// reduction as k_finish_sum, so every block of a kernel that needs a scalar forms it bitwise
+// alike (and alike to a separate finishing kernel).  sh holds 33 values.
+__device__ __forceinline__ double partials_total(const double* __restrict__ part, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < RB; i += blockDim.x) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) sh[32] = s;
+  __syncthreads();
+  const double t = sh[32];
+  __syncthreads();
+  return t;
+}
+
 template <typename A, typename B>
 __global__ void __launch_bounds__(RT) k_dot(const A* __restrict__ a, const B* __restrict__ b,
                                             long long n, long long stride,
@@ -131,34 +145,6 @@ cudaError_t launch_mask_copy(const double* a, double* b, const uint8_t* nmask, l
 }
 
 // --------------------------------------------------------------------------- FCG steps
-// beta = -(z^T q_prev) / (p_prev^T q_prev); zero on the first step after a (re)start
-__global__ void k_scalar_beta(FcgScalars* sc, const double* __restrict__ zq) {
-  FcgScalars& c = sc[threadIdx.x];
-  if (!c.active) return;
-  c.zq = zq[threadIdx.x];
-  c.beta = c.restart ? 0.0 : -c.zq / c.pq_prev;
-  c.restart = 0;
-}
-
-// p = z + beta p  (PT = float in MIXED mode, double in FP64 mode)
-template <typename PT>
-__global__ void __launch_bounds__(RT) k_pupdate(const PT* __restrict__ z, PT* __restrict__ p,
-                                                long long n, long long stride,
-                                                const FcgScalars* __restrict__ sc) {
-  const FcgScalars& c = sc[blockIdx.y];
-  if (!c.active) return;
-  z += blockIdx.y * stride;
-  p += blockIdx.y * stride;
-  const double beta = c.beta;
-  if (beta == 0.0) {   // (re)start: p = z (p may hold stale or uninitialised data)
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
-      p[i] = z[i];
-    return;
-  }
-  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
-    p[i] = (PT)((double)z[i] + beta * (double)p[i]);
-}
-
 // partial sums of p^T q and p^T r in one pass
 template <typename PT>
 __global__ void __launch_bounds__(RT) k_pq_pr(const PT* __restrict__ p, const PT* __restrict__ q,
@@ -184,42 +170,67 @@ __global__ void __launch_bounds__(RT) k_pq_pr(const PT* __restrict__ p, const PT
   }
 }
 
-__global__ void k_scalar_alpha(FcgScalars* sc, const double* __restrict__ partials) {
-  __shared__ double sh[32];
-  FcgScalars& c = sc[blockIdx.x];
+// p = z + beta p with beta = -(z^T q_prev) / (p_prev^T q_prev) formed in every block from the
+// partials of z^T q (zero on the first step): the finishing sum and the scalar step of the
+// recurrence fused into the update.  Block 0 records z^T q and beta.
+template <typename PT>
+__global__ void __launch_bounds__(RT) k_pupdate_beta(const PT* __restrict__ z, PT* __restrict__ p,
+                                                     long long n, long long stride,
+                                                     const double* __restrict__ zq_part,
+                                                     FcgScalars* __restrict__ sc) {
+  __shared__ double sh[33];
+  FcgScalars& c = sc[blockIdx.y];
   if (!c.active) return;
-  double s1 = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < RB; i += blockDim.x) {
-    s1 += partials[(blockIdx.x * 2 + 0) * RB + i];
-    s2 += partials[(blockIdx.x * 2 + 1) * RB + i];
+  const double zq = partials_total(zq_part + (long long)blockIdx.y * RB, sh);
+  const double beta = c.restart ? 0.0 : -zq / c.pq_prev;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.zq = zq;
+    c.beta = beta;
   }
-  s1 = block_sum(s1, sh);
-  s2 = block_sum(s2, sh);
-  if (threadIdx.x == 0) {
-    c.pq = s1;
-    c.pr = s2;
-    if (!(s1 > 0.0) || !isfinite(s1) || !isfinite(s2)) {
-      c.status = isfinite(s1) && isfinite(s2) ? MSTOPO_NOT_SPD : MSTOPO_NONFINITE;
+  z += blockIdx.y * stride;
+  p += blockIdx.y * stride;
+  if (beta == 0.0) {   // (re)start: p = z (p may hold stale or uninitialised data)
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
+      p[i] = z[i];
+    return;
+  }
+  for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)RB * RT)
+    p[i] = (PT)((double)z[i] + beta * (double)p[i]);
+}
+
+// alpha = p^T r / p^T q formed in every block from the partials (a breakdown p^T q <= 0 or a
+// non-finite value stops the system in every block alike), then x += alpha p, r -= alpha q,
+// (MIXED: r32 = float(r)) and the partials of ||r||^2 into rr_part.  Block 0 records the
+// scalars and ends the first-step state.
+template <typename PT>
+__global__ void __launch_bounds__(RT) k_xr_alpha(double* __restrict__ x, double* __restrict__ r,
+                                                 float* __restrict__ r32, const PT* __restrict__ p,
+                                                 const PT* __restrict__ q, long long n,
+                                                 long long stride,
+                                                 const double* __restrict__ pqr_part,
+                                                 double* __restrict__ rr_part,
+                                                 FcgScalars* __restrict__ sc) {
+  __shared__ double sh[33];
+  FcgScalars& c = sc[blockIdx.y];
+  if (!c.active) return;
+  const double pq = partials_total(pqr_part + (long long)(blockIdx.y * 2 + 0) * RB, sh);
+  const double pr = partials_total(pqr_part + (long long)(blockIdx.y * 2 + 1) * RB, sh);
+  const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(pr);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.pq = pq;
+    c.pr = pr;
+    c.restart = 0;
+    if (bad) {
+      c.status = isfinite(pq) && isfinite(pr) ? MSTOPO_NOT_SPD : MSTOPO_NONFINITE;
       c.active = 0;
       c.alpha = 0.0;
     } else {
-      c.alpha = s2 / s1;
-      c.pq_prev = s1;
+      c.alpha = pr / pq;
+      c.pq_prev = pq;
     }
   }
-}
-
-// x += alpha p ; r -= alpha q ; (MIXED: r32 = float(r)) ; partial ||r||^2
-template <typename PT>
-__global__ void __launch_bounds__(RT) k_xr_update(double* __restrict__ x, double* __restrict__ r,
-                                                  float* __restrict__ r32,
-                                                  const PT* __restrict__ p,
-                                                  const PT* __restrict__ q, long long n,
-                                                  long long stride, double* __restrict__ partials,
-                                                  const FcgScalars* __restrict__ sc) {
-  __shared__ double sh[32];
-  if (!sc[blockIdx.y].active) return;
-  const double alpha = sc[blockIdx.y].alpha;
+  if (bad) return;
+  const double alpha = pr / pq;
   x += blockIdx.y * stride;
   r += blockIdx.y * stride;
   p += blockIdx.y * stride;
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(RT) k_xr_update(double* __restrict__ x, double
     s = fma(rv, rv, s);
   }
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) partials[blockIdx.y * RB + blockIdx.x] = s;
+  if (threadIdx.x == 0) rr_part[blockIdx.y * RB + blockIdx.x] = s;
 }
 
 __global__ void k_scalar_rr(FcgScalars* sc, const double* __restrict__ partials, double tol2) {
@@ -490,11 +501,8 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
     if (s2 != MSTOPO_OK) return s2;
     if (mixed) CK(launch_dot_partials_f32(sv.z32, sv.q32, n, nsys, n, sv.partials, h->s));
     else CK(launch_dot_partials(sv.z64, sv.q64, n, nsys, n, sv.partials, h->s));
-    CK(launch_finish_sum(sv.partials, nsys, vtmp, h->s));
-    note_launch(), k_scalar_beta<<<1, nsys, 0, h->s>>>(sv.sc, vtmp);
-    CK(cudaGetLastError());
     if (mixed) {
-      note_launch(), k_pupdate<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.sc);
+      note_launch(), k_pupdate_beta<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z32, sv.p32, n, n, sv.partials, sv.sc);
       CK(cudaGetLastError());
       cudaEvent_t pa = prof_begin(h->prof, h->s);
       CK(launch_matvec_f32(sv.p32, sv.q32, E32, h->d_nmask, h->nelx, h->nely, h->st32, nsys, n,
@@ -502,7 +510,7 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
       prof_end(h->prof, PROF_MATVEC32, pa, h->s);
       note_launch(), k_pq_pr<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p32, sv.q32, sv.r, n, n, sv.partials, sv.sc);
     } else {
-      note_launch(), k_pupdate<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.sc);
+      note_launch(), k_pupdate_beta<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.z64, sv.p64, n, n, sv.partials, sv.sc);
       CK(cudaGetLastError());
       cudaEvent_t pa = prof_begin(h->prof, h->s);
       CK(launch_matvec_f64(sv.p64, sv.q64, E64, h->d_nmask, h->nelx, h->nely, h->st64, nsys, n,
@@ -511,16 +519,16 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
       note_launch(), k_pq_pr<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.p64, sv.q64, sv.r, n, n, sv.partials, sv.sc);
     }
     CK(cudaGetLastError());
-    note_launch(), k_scalar_alpha<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials);
-    CK(cudaGetLastError());
+    // ||r||^2 partials after the p^T q, p^T r ones (the fused update still reads those)
+    double* rr_part = sv.partials + (size_t)MSTOPO_MAX_SYS * 2 * RB;
     if (mixed)
-      note_launch(), k_xr_update<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
-                                                          sv.partials, sv.sc);
+      note_launch(), k_xr_alpha<float><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, sv.r32, sv.p32, sv.q32, n, n,
+                                                         sv.partials, rr_part, sv.sc);
     else
-      note_launch(), k_xr_update<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
-                                                           n, sv.partials, sv.sc);
+      note_launch(), k_xr_alpha<double><<<dim3(RB, nsys), RT, 0, h->s>>>(sv.x, sv.r, nullptr, sv.p64, sv.q64, n,
+                                                          n, sv.partials, rr_part, sv.sc);
     CK(cudaGetLastError());
-    note_launch(), k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, sv.partials, tol2);
+    note_launch(), k_scalar_rr<<<nsys, RT, 0, h->s>>>(sv.sc, rr_part, tol2);
     CK(cudaGetLastError());
     return MSTOPO_OK;
   };
