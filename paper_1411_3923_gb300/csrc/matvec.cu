@@ -370,112 +370,48 @@ __device__ __forceinline__ void pair_force(const Row4& b, const Row4& m, const R
   node_force<float>(b1, m1, t1, eb.a, eb.b, et.a, et.b, c, ax1, ay1);
 }
 
-// The same forces with the two nodes' arithmetic paired: every (node i0, node i0+1) pair of
-// terms goes through one paired FP32 operation (the stencil coefficients are the same for both
-// nodes).  Each paired FMA rounds exactly like the two scalar ones in the same order, so the
-// results are bitwise those of pair_force.
-struct StencilPair { float2 c[4][3][4]; };    // (c, c) pairs of the FP32 stencil coefficients
-struct Row4P { float2 xLA, xAB, xBR, yLA, yAB, yBR; };   // (node i0's, node i0+1's) neighbours
-struct ERowP { float2 la, ab; };              // element moduli: (i0-1, i0) and (i0, i0+1)
-
-__device__ __forceinline__ void pair_row(const Row4& w, Row4P& q) {
-  q.xLA = make_float2(w.L.x, w.A.x); q.xAB = make_float2(w.A.x, w.B.x); q.xBR = make_float2(w.B.x, w.R.x);
-  q.yLA = make_float2(w.L.y, w.A.y); q.yAB = make_float2(w.A.y, w.B.y); q.yBR = make_float2(w.B.y, w.R.y);
-}
-__device__ __forceinline__ void pair_erow(const ERow& e, ERowP& q) {
-  q.la = make_float2(e.l, e.a);
-  q.ab = make_float2(e.a, e.b);
-}
-__device__ __forceinline__ void blk2(float2& ax, float2& ay, const float2 (&b)[4], float2 dx, float2 dy) {
-  ax = __ffma2_rn(b[0], dx, ax); ax = __ffma2_rn(b[1], dy, ax);
-  ay = __ffma2_rn(b[2], dx, ay); ay = __ffma2_rn(b[3], dy, ay);
-}
-
-__device__ __forceinline__ void pair_force2(const Row4P& b, const Row4P& m, const Row4P& t,
-                                            const ERowP& eb, const ERowP& et, const StencilPair& c,
-                                            float2& yx, float2& yy) {
-  const float2 m1 = make_float2(-1.f, -1.f);
-  const float2 cx = m.xAB, cy = m.yAB;    // the two centres
-  // neighbour - centre, as -1 * centre + neighbour (one rounding, as the subtraction)
-  const float2 d00x = __ffma2_rn(cx, m1, b.xLA), d00y = __ffma2_rn(cy, m1, b.yLA);
-  const float2 d01x = __ffma2_rn(cx, m1, b.xAB), d01y = __ffma2_rn(cy, m1, b.yAB);
-  const float2 d02x = __ffma2_rn(cx, m1, b.xBR), d02y = __ffma2_rn(cy, m1, b.yBR);
-  const float2 d10x = __ffma2_rn(cx, m1, m.xLA), d10y = __ffma2_rn(cy, m1, m.yLA);
-  const float2 d12x = __ffma2_rn(cx, m1, m.xBR), d12y = __ffma2_rn(cy, m1, m.yBR);
-  const float2 d20x = __ffma2_rn(cx, m1, t.xLA), d20y = __ffma2_rn(cy, m1, t.yLA);
-  const float2 d21x = __ffma2_rn(cx, m1, t.xAB), d21y = __ffma2_rn(cy, m1, t.yAB);
-  const float2 d22x = __ffma2_rn(cx, m1, t.xBR), d22y = __ffma2_rn(cy, m1, t.yBR);
-  const float2 z = make_float2(0.f, 0.f);
-  float2 ax = z, ay = z;
-  yx = z;
-  yy = z;
-  // LL element (node i0: elements (i0-1, i0) of the row below, node i0+1: (i0, i0+1))
-  blk2(ax, ay, c.c[0][0], d00x, d00y); blk2(ax, ay, c.c[0][1], d01x, d01y); blk2(ax, ay, c.c[0][2], d10x, d10y);
-  yx = __ffma2_rn(eb.la, ax, yx); yy = __ffma2_rn(eb.la, ay, yy);
-  ax = z; ay = z;   // LR element
-  blk2(ax, ay, c.c[1][0], d01x, d01y); blk2(ax, ay, c.c[1][1], d02x, d02y); blk2(ax, ay, c.c[1][2], d12x, d12y);
-  yx = __ffma2_rn(eb.ab, ax, yx); yy = __ffma2_rn(eb.ab, ay, yy);
-  ax = z; ay = z;   // UL element
-  blk2(ax, ay, c.c[2][0], d10x, d10y); blk2(ax, ay, c.c[2][1], d21x, d21y); blk2(ax, ay, c.c[2][2], d20x, d20y);
-  yx = __ffma2_rn(et.la, ax, yx); yy = __ffma2_rn(et.la, ay, yy);
-  ax = z; ay = z;   // UR element
-  blk2(ax, ay, c.c[3][0], d12x, d12y); blk2(ax, ay, c.c[3][1], d22x, d22y); blk2(ax, ay, c.c[3][2], d21x, d21y);
-  yx = __ffma2_rn(et.ab, ax, yx); yy = __ffma2_rn(et.ab, ay, yy);
-}
-
 template <bool MASK_IN, bool FAST>
 __device__ __forceinline__ void matvec2_strip(const float* __restrict__ u, float* __restrict__ y,
                                               const float* __restrict__ E,
                                               const uint8_t* __restrict__ nmask, int nelx,
-                                              int nely, const StencilPair& c, int i0,
+                                              int nely, const StencilCoef<float>& c, int i0,
                                               int j0, int lane) {
   const int nx1 = nelx + 1, ny1 = nely + 1;
   Pend2 p0, p1, p2;
   issue2<MASK_IN, FAST>(p0, u, E, nmask, i0, lane, j0 - 1, nelx, nely);
   issue2<MASK_IN, FAST>(p1, u, E, nmask, i0, lane, j0, nelx, nely);
-  Row4 w;
-  Row4P w0, w1, w2;
-  ERow er, dummy;
-  ERowP e0, e1, e2;
-  make_row2(p0, lane, w, dummy);
-  pair_row(w, w0);
-  make_row2(p1, lane, w, er);       // element row j0-1
-  pair_row(w, w1);
-  pair_erow(er, e0);
+  Row4 w0, w1, w2;
+  ERow e0, e1, e2, dummy;
+  make_row2(p0, lane, w0, dummy);
+  make_row2(p1, lane, w1, e0);     // e0 = element row j0-1
   const int jend = min(j0 + MV_TY, ny1);
   issue2<MASK_IN, FAST>(p0, u, E, nmask, i0, lane, j0 + 1, nelx, nely);
   issue2<MASK_IN, FAST>(p1, u, E, nmask, i0, lane, j0 + 2, nelx, nely);
   issue2<MASK_IN, FAST>(p2, u, E, nmask, i0, lane, j0 + 3, nelx, nely);
-  auto emit = [&](int j, uint8_t fa, uint8_t fb, float2 yx, float2 yy) {
+  auto emit = [&](int j, uint8_t fa, uint8_t fb, float x0, float y0, float x1, float y1) {
     if (j < jend) {
       float2* yr = reinterpret_cast<float2*>(y) + (long long)j * nx1;
-      if (i0 < nx1) yr[i0] = make_float2((fa & 1) ? 0.f : yx.x, (fa & 2) ? 0.f : yy.x);
-      if (i0 + 1 < nx1) yr[i0 + 1] = make_float2((fb & 1) ? 0.f : yx.y, (fb & 2) ? 0.f : yy.y);
+      if (i0 < nx1) yr[i0] = make_float2((fa & 1) ? 0.f : x0, (fa & 2) ? 0.f : y0);
+      if (i0 + 1 < nx1) yr[i0 + 1] = make_float2((fb & 1) ? 0.f : x1, (fb & 2) ? 0.f : y1);
     }
   };
   for (int jb = j0; jb < jend; jb += 3) {
-    float2 yx, yy;
-    make_row2(p0, lane, w, er);
-    pair_row(w, w2);
-    pair_erow(er, e1);
+    float x0, y0, x1, y1;
+    make_row2(p0, lane, w2, e1);
     uint8_t fa = p0.ma, fb = p0.mb;
     if (jb + 4 <= jend + 1) issue2<MASK_IN, FAST>(p0, u, E, nmask, i0, lane, jb + 4, nelx, nely);
-    pair_force2(w0, w1, w2, e0, e1, c, yx, yy);
-    emit(jb, fa, fb, yx, yy);
-    make_row2(p1, lane, w, er);
-    pair_row(w, w0);
-    pair_erow(er, e2);
+    pair_force(w0, w1, w2, e0, e1, c, x0, y0, x1, y1);
+    emit(jb, fa, fb, x0, y0, x1, y1);
+    make_row2(p1, lane, w0, e2);
     fa = p1.ma; fb = p1.mb;
     if (jb + 5 <= jend + 1) issue2<MASK_IN, FAST>(p1, u, E, nmask, i0, lane, jb + 5, nelx, nely);
-    pair_force2(w1, w2, w0, e1, e2, c, yx, yy);
-    emit(jb + 1, fa, fb, yx, yy);
-    make_row2(p2, lane, w, er);
-    pair_row(w, w1);
-    pair_erow(er, e0);
+    pair_force(w1, w2, w0, e1, e2, c, x0, y0, x1, y1);
+    emit(jb + 1, fa, fb, x0, y0, x1, y1);
+    make_row2(p2, lane, w1, e0);
     fa = p2.ma; fb = p2.mb;
     if (jb + 6 <= jend + 1) issue2<MASK_IN, FAST>(p2, u, E, nmask, i0, lane, jb + 6, nelx, nely);
-    pair_force2(w2, w0, w1, e2, e0, c, yx, yy);
-    emit(jb + 2, fa, fb, yx, yy);
+    pair_force(w2, w0, w1, e2, e0, c, x0, y0, x1, y1);
+    emit(jb + 2, fa, fb, x0, y0, x1, y1);
   }
 }
 
@@ -484,7 +420,7 @@ __global__ void __launch_bounds__(MV_TX) k_matvec2(const float* __restrict__ u,
                                                    float* __restrict__ y,
                                                    const float* __restrict__ E,
                                                    const uint8_t* __restrict__ nmask, int nelx,
-                                                   int nely, StencilPair c,
+                                                   int nely, StencilCoef<float> c,
                                                    long long vec_stride, long long e_stride) {
   const int lane = threadIdx.x & 31;
   const int c0 = blockIdx.x * MV_TX * 2;           // first node column of the block
@@ -507,14 +443,10 @@ cudaError_t launch_matvec_f32(const float* u, float* y, const float* E, const ui
                               long long vec_stride, long long e_stride, cudaStream_t s,
                               bool mask_input) {
   dim3 grid(cdiv(nelx + 1, 2 * MV_TX), cdiv(nely + 1, MV_TY), nsys);
-  StencilPair cp;
-  for (int e = 0; e < 4; ++e)
-    for (int m = 0; m < 3; ++m)
-      for (int q = 0; q < 4; ++q) cp.c[e][m][q] = make_float2(c.c[e][m][q], c.c[e][m][q]);
   if (mask_input)
-    note_launch(), k_matvec2<true><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, cp, vec_stride, e_stride);
+    note_launch(), k_matvec2<true><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
   else
-    note_launch(), k_matvec2<false><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, cp, vec_stride, e_stride);
+    note_launch(), k_matvec2<false><<<grid, MV_TX, 0, s>>>(u, y, E, nmask, nelx, nely, c, vec_stride, e_stride);
   return cudaGetLastError();
 }
 
