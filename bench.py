@@ -630,6 +630,11 @@ def run_workload(args):
         c, fr, g = prob.compliance_and_sensitivity(1.0)
         torch.cuda.synchronize()
         t4 = time.time()
+        # one more solve with per-kernel events (graphs off): where the solve's time goes
+        prob.set_profiling(True)
+        _, infos_p = prob.solve(f, -1)
+        st = prob.stats()
+        prob.set_profiling(False)
         out[prec] = {"build_s": t1 - t0, "build": {k: info[k] for k in ("n_agglomerates", "n_types", "n_coarse",
                                                                         "coarse_solver", "ms_eigen", "ms_patch_factor",
                                                                         "ms_coarse", "ms_total")},
@@ -637,7 +642,12 @@ def run_workload(args):
                      "iterations": [i["iterations"] for i in infos],
                      "rel_residual": [i["rel_residual"] for i in infos],
                      "compliance": [i["compliance"] for i in infos], "f_robust": fr,
-                     "sensitivity_s": t4 - t3}
+                     "sensitivity_s": t4 - t3,
+                     "profiled_solve": {"event_ms": infos_p[0]["ms"],
+                                        "kernels_ms": {k: v["ms"] for k, v in st.items()
+                                                       if isinstance(v, dict) and "ms" in v},
+                                        "launches": {k: v["launches"] for k, v in st.items()
+                                                     if isinstance(v, dict) and "launches" in v}}}
         prob.close()
         del prob
         torch.cuda.empty_cache()
@@ -660,7 +670,8 @@ def run_only(args):
     name = args.only_workload or (WORKLOAD if args.only in ("patch", "solve") else "mbb_c5")
     wl = workloads.make(name, args.only_scale)
     prob = m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
-                     penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision="mixed")
+                     penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision="mixed",
+                     patch_kernel=args.patch_kernel)
     prob.set_design(torch.from_numpy(wl.rho).to(dev), wl.rmin, wl.beta, wl.etas, wl.cell)
     if args.only == "patch":
         prob.build_preconditioner(-1)

@@ -71,10 +71,14 @@ typedef enum {
                                      it unchanged. No patch factors are built. */
 } mstopo_preconditioner;
 
+/* Kernel of the FP32 patch solves (MIXED).  The tensor-core kernel (H = 8, 16, 32 only) takes
+ * up to 128 patches of one type as the rows of each MMA (TF32 high and low parts of both
+ * operands); it wins when a launch holds many patches per type.  AUTO compares the two by a
+ * measured cost per wave; TENSOR_CORES with another H makes the build fail with INVALID_ARG. */
 typedef enum {
-  MSTOPO_PATCH_AUTO = 0,           /* by problem size: the tensor cores from 128 patch solves per SM */
+  MSTOPO_PATCH_AUTO = 0,           /* the cheaper by the cost model, per build                  */
   MSTOPO_PATCH_CUDA_CORES = 1,     /* FP32 and FP64 patch solves on the CUDA cores              */
-  MSTOPO_PATCH_TENSOR_CORES = 2    /* MIXED: FP32 patch solves on the tensor cores (TF32 pairs) */
+  MSTOPO_PATCH_TENSOR_CORES = 2    /* MIXED: FP32 patch solves on the tensor cores              */
 } mstopo_patch_kernel;
 
 typedef enum {

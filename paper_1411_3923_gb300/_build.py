@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmstopo.so")
-SOURCES = ["api.cu", "matvec.cu", "design.cu", "krylov.cu", "precond.cu", "patch_tc.cu", "patch_tri.cu", "smoother.cu", "coarse.cu", "gmres.cu", "pde_filter.cu", "optimise.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "matvec.cu", "design.cu", "krylov.cu", "precond.cu", "patch_tri.cu", "patch_twtc.cu", "smoother.cu", "coarse.cu", "gmres.cu", "pde_filter.cu", "optimise.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -148,7 +148,7 @@ struct Precond {
   int* d_kept = nullptr;            // [n_types]
   int* d_coff = nullptr;            // [Nc+1] coarse-unknown offsets
   // patch-solve work groups: [0] FP32 on the CUDA cores, [1] FP32 on the tensor cores
-  // (PATCH_COLS patches per group), [2] FP64 (at most 4 patches per group)
+  // (TW_M patches per group), [2] FP64 (at most 4 patches per group)
   PatchGroups pg[3];
   int nsv = 0;                      // realisations with their own operators
   // per-system patch matrices: block tridiagonal by node rows of the (2H+1)^2 agglomerate
@@ -159,10 +159,11 @@ struct Precond {
   // [T*nsv][patch_tri_system_elems]
   double* d_tri64 = nullptr;
   float* d_tri32 = nullptr;
-// tensor-core FP32 patch solve (csrc/patch_tc.cu): TF32 hi/lo factor lines [T][2][NL][line]
-  unsigned char* d_ptc = nullptr;
-  long long tc_line_bytes = 0;
-  int patch_tc = 0;
+  // tensor-core FP32 patch solves on the two-sided elimination (csrc/patch_twtc.cu): packed
+  // blocks [T*nsv][TwGeom::SS bytes] and the middle-line exchange [groups][2][TW_M][nbP]
+  unsigned char* d_ptw = nullptr;
+  float* d_twu = nullptr;
+  int patch_tc = 0;                 // FP32 patch solves on the tensor cores
   int kind = 0;                     // mstopo_preconditioner
   void* d_sgs = nullptr;            // multiplicative SGS: [2][MSTOPO_MAX_SYS][n_dof] doubles of work space
   // per-type eigenpairs: lambda [T][kmax], Psi [T][NA*NA][2][kmax]
@@ -342,12 +343,29 @@ cudaError_t patch_tri_solve_f32(mstopo_handle* h, const PatchGroups& G, const fl
 cudaError_t patch_tri_solve_f64(mstopo_handle* h, const PatchGroups& G, const double* r, int sys0,
                                 int nsys, double* Xg);
 
-// tensor-core FP32 patch solve (csrc/patch_tc.cu)
-long long patch_tc_line_bytes(int nb);
-size_t patch_tc_smem(int nb, int nst);
-cudaError_t patch_tc_pack(const double* Linv, const double* W, const double* V, int T, int nb,
-                          int NL, unsigned char* out, cudaStream_t s);
-cudaError_t patch_tc_solve(mstopo_handle* h, int Q, const float* r, int sys0, int nsys, float* Xg);
+// tensor-core FP32 patch solves on the two-sided elimination (csrc/patch_twtc.cu): 128
+// patches of one type and realisation per cluster of two CTAs.  Per packed block: KS K-steps of
+// [TF32 hi tile | lo tile] of the symmetric inverse (npad rows x 8 columns each, core matrices
+// of 8 rows x 16 B), then the FP32 couplings: a chain block [C][C^T], the middle block
+// [C_0][C_1][C_0^T][C_1^T], each [4 KS nodes][2][6] (zero beyond nb).
+struct TwGeom {
+  int nb, npad, ks;          // DOFs per line, MMA N (a multiple of 16, >= nb), K-steps of 8
+  int tile;                  // bytes of one tile (npad x 8 TF32)
+  int cpl;                   // byte offset of the couplings in a block
+  int cset;                  // bytes of one coupling set (6 x 8 KS FP32)
+  long long LB, LBM, SS;     // bytes of a chain block, of the middle block, of a patch system
+};
+constexpr int TW_M = 128;    // patches per group of the tensor-core kernel
+TwGeom patch_twtc_geometry(int nb, int NL);
+// supported line sizes (the kernel is compiled for a few K-step counts) and shared memory
+bool patch_twtc_ok(int nb);
+// the tensor-core pack from the FP64 CUDA-core pack of the same systems
+cudaError_t patch_twtc_pack(const double* tri64, int nsys, int nb, int NL, unsigned char* out,
+                            cudaStream_t s);
+// X: [group][NL][TW_M][nb] results; U: [group][2][TW_M][nb] exchange of the middle line
+cudaError_t patch_twtc_solve(mstopo_handle* h, const PatchGroups& G, const float* r, int sys0,
+                             int nsys, float* Xg, float* U);
+
 // the paper's multiplicative SGS two-level preconditioner (csrc/smoother.cu); part 0 = the
 // operator, 2 = one symmetric sweep from zero
 cudaError_t sgs_apply_f64(mstopo_handle* h, const double* r, double* z, int sys0, int nsys, int part);

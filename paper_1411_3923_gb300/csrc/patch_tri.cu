@@ -59,6 +59,7 @@
 
 #include "blocktri.cuh"
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -200,6 +201,59 @@ __global__ void k_patch_tri_pack(const double* __restrict__ Lt, const double* __
     }
     if (out64) out64[o + t] = v;
     if (out32) out32[o + t] = (float)v;
+  }
+}
+
+// The tensor-core kernel's blocks (csrc/patch_twtc.cu) from the FP64 pack of the same system:
+// the symmetric inverse as TF32 hi/lo tiles (B[n][k] = S^-1[n][k], zero beyond nb; the lower
+// triangle of the pack read across the diagonal where a row stores fewer columns), and every
+// coupling C with its transpose CT, K[q][c] = the coefficient of neighbour DOF 2(c/2) - 2 + q in
+// row c: CT[2 dn + 2 + f][2a + e] = C[2 - 2 dn + e][2 (a + dn) + f] (zero outside the line), so
+// that both sweeps apply a coupling with the same six-term stencil; stored per node a as
+// [e][q] (12 floats), the pairs (q, q + 1) of one row adjacent.
+__global__ void k_patch_twtc_pack(const double* __restrict__ tri64, TriGeom g, TwGeom w, int NL,
+                                  unsigned char* __restrict__ out) {
+  const int sys = blockIdx.x, b = blockIdx.y;
+  const int H = (NL - 1) / 2, nb = g.nb, NN = nb / 2;
+  const bool mid = b == 2 * H;
+  const double* blk = tri64 + (long long)sys * g.SS + (long long)b * g.LB;
+  unsigned char* ob = out + (long long)sys * w.SS + (long long)b * w.LB;
+  auto S = [&](int r, int c) -> double {
+    const int I = r >> 5;
+    const int width = I < g.nfull ? 32 * (I + 1) : nb;
+    if (c >= width) {
+      const int t = r; r = c; c = t;
+    }
+    return blk[tri_rowoff(g, r) + c];
+  };
+  const int te = w.npad * 8;
+  for (int t = threadIdx.x; t < w.ks * te; t += blockDim.x) {
+    const int k = t / te, e = t % te;
+    const int n = e >> 3, kk = e & 7, c = 8 * k + kk;
+    const double v = (n < nb && c < nb) ? S(n, c) : 0.0;
+    const uint32_t hi = tf32_rna((float)v);
+    const uint32_t lo = tf32_rna((float)(v - (double)__uint_as_float(hi)));
+    const int o = k * 2 * w.tile + (n >> 3) * 256 + (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4;
+    *reinterpret_cast<uint32_t*>(ob + o) = hi;
+    *reinterpret_cast<uint32_t*>(ob + o + w.tile) = lo;
+  }
+  const int nsets = mid ? 2 : 1, KP = 8 * w.ks;
+  float* cp = reinterpret_cast<float*>(ob + w.cpl);
+  for (int t = threadIdx.x; t < 2 * nsets * 6 * KP; t += blockDim.x) {
+    // set element (node a, DOF e of the node, term q) = K[q][2a + e], 12 floats per node
+    const int set = t / (6 * KP), u = t % (6 * KP), q = u % 6, c = u / 6;
+    const bool tr = set >= nsets;
+    const double* C = blk + g.TB + (long long)(tr ? set - nsets : set) * 6 * nb;
+    double v = 0.0;
+    if (c < nb) {
+      if (!tr) {
+        v = C[q * nb + c];
+      } else {
+        const int a = c >> 1, e = c & 1, dn = (q >> 1) - 1, f = q & 1, n = a + dn;
+        v = (n >= 0 && n < NN) ? C[(2 - 2 * dn + e) * nb + 2 * n + f] : 0.0;
+      }
+    }
+    cp[t] = (float)v;
   }
 }
 
@@ -685,6 +739,28 @@ cudaError_t patch_tri_pack(const double* Lt, const double* Bt, const double* Lr,
   const TriGeom g = tri_geometry(nb, NL);
   note_launch(), k_patch_tri_pack<<<dim3(nsys, NL), 256, 0, s>>>(Lt, Bt, Lr, Br, Lm, NL, NLr, g,
                                                                  out64, out32);
+  return cudaGetLastError();
+}
+
+TwGeom patch_twtc_geometry(int nb, int NL) {
+  TwGeom w{};
+  w.nb = nb;
+  w.npad = (nb + 15) / 16 * 16;
+  w.ks = (nb + 7) / 8;
+  w.tile = w.npad * 32;
+  w.cpl = w.ks * 2 * w.tile;
+  w.cset = 6 * 8 * w.ks * 4;
+  w.LB = (long long)w.cpl + 2LL * w.cset;
+  w.LBM = (long long)w.cpl + 4LL * w.cset;
+  w.SS = (long long)(NL - 1) * w.LB + w.LBM;
+  return w;
+}
+
+cudaError_t patch_twtc_pack(const double* tri64, int nsys, int nb, int NL, unsigned char* out,
+                            cudaStream_t s) {
+  const TriGeom g = tri_geometry(nb, NL);
+  const TwGeom w = patch_twtc_geometry(nb, NL);
+  note_launch(), k_patch_twtc_pack<<<dim3(nsys, NL), 256, 0, s>>>(tri64, g, w, NL, out);
   return cudaGetLastError();
 }
 

@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(256) k_combine(
     const int* __restrict__ type_of, const int* __restrict__ kept, const int* __restrict__ coff,
     const T* __restrict__ psi, int kmax, const double* __restrict__ uc, int Nt,
     const int* __restrict__ agg_group, const int* __restrict__ agg_slot, const T* __restrict__ Xg,
-    int R, const uint8_t* __restrict__ nmask, int part) {
+    int R, int pfast, const uint8_t* __restrict__ nmask, int part) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   const int s = blockIdx.z;
@@ -930,7 +930,10 @@ __global__ void __launch_bounds__(256) k_combine(
       if (part != 1) {
         const long long gi = (long long)(sys0 + s) * Nc + i;
         const int col = agg_slot[gi];
-        const long long base = (((long long)agg_group[gi] * N + lb) * R + col) * nbP + 2 * la;
+        // work-buffer layout [group][line][column][DOF], or [group][line][node][column][2]
+        // (pfast: the tensor-core kernel's, consecutive columns = consecutive patches)
+        const long long gl = (long long)agg_group[gi] * N + lb;
+        const long long base = pfast ? ((gl * (nbP / 2) + la) * R + col) * 2 : (gl * R + col) * nbP + 2 * la;
         zx += Xg[base];
         zy += Xg[base + 1];
       }
@@ -940,31 +943,6 @@ __global__ void __launch_bounds__(256) k_combine(
   const uint8_t f = nmask[node];
   z[s * stride + 2 * node] = (f & 1) ? T(0) : zx;
   z[s * stride + 2 * node + 1] = (f & 2) ? T(0) : zy;
-}
-
-// W_k = Linv_k C_{k-1} (k >= 1) and V_k = Linv_k^T C_k^T (k <= NL-2), FP64, one CTA per
-// (type, line, which); zero where undefined.
-__global__ void __launch_bounds__(PC_THREADS) k_patch_wv(const double* __restrict__ Linv,
-                                                         const double* __restrict__ C,
-                                                         double* __restrict__ W,
-                                                         double* __restrict__ V, int nb, int NL) {
-  const int type = blockIdx.x, k = blockIdx.y, which = blockIdx.z;
-  const long long nn = (long long)nb * nb;
-  const double* Lk = Linv + ((long long)type * NL + k) * nn;
-  double* out = (which == 0 ? W : V) + ((long long)type * NL + k) * nn;
-  const bool defined = which == 0 ? (k >= 1) : (k <= NL - 2);
-  const double* Cm = defined ? C + ((long long)type * (NL - 1) + (which == 0 ? k - 1 : k)) * nn : nullptr;
-  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-    const int i = t / nb, j = t % nb;
-    double s = 0.0;
-    if (defined) {
-      if (which == 0)
-        for (int l = 0; l <= i; ++l) s = fma(Lk[i * nb + l], Cm[l * nb + j], s);
-      else
-        for (int l = i; l < nb; ++l) s = fma(Lk[l * nb + i], Cm[j * nb + l], s);
-    }
-    out[t] = s;
-  }
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -985,7 +963,7 @@ void precond_free(Precond& pc) {
     dfree(G.d_perm); dfree(G.d_type); dfree(G.d_first); dfree(G.d_count); dfree(G.d_sys); dfree(G.d_agg);
   }
   dfree(pc.d_pfree);
-  dfree(pc.d_tri64); dfree(pc.d_tri32); dfree(pc.d_ptc);
+  dfree(pc.d_tri64); dfree(pc.d_tri32); dfree(pc.d_ptw); dfree(pc.d_twu);
   dfree(pc.d_lambda); dfree(pc.d_psi64); dfree(pc.d_psi32); dfree(pc.d_eigres); dfree(pc.d_eigsweeps);
   dfree(pc.d_Kc); dfree(pc.d_Kcinv);
   dfree(pc.d_cLinv); dfree(pc.d_cLinvT); dfree(pc.d_cW); dfree(pc.d_cV);
@@ -1194,6 +1172,8 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   // Measured on the 1024x512 workload (time per wave relative to a full R = 4 wave, three CTAs
   // per SM): R = 8 0.77, R = 16 1.44.  Fewer columns win ties.
   int P = 4;
+  double tri_waves = 0.0;   // the chosen CUDA-core configuration in R = 4 wave units
+  long long tw_groups = 0;  // groups of the tensor-core kernel (TW_M patches of one type)
   {
     std::vector<long long> per_type(T, 0);
     for (int i = 0; i < pc.Nc; ++i) per_type[pc.h_type_of_agg[i]]++;
@@ -1211,6 +1191,9 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
         P = cols[c];
       }
     }
+    tri_waves = best;
+    for (int t = 0; t < T; ++t) tw_groups += (per_type[t] + TW_M - 1) / TW_M;
+    tw_groups *= nsv;
   }
   if (!patch_tri_assignment_ok(nbP)) {
     h->err = "H > 32 is not supported by the patch solve";
@@ -1253,14 +1236,24 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
         h->err = "patch matrix not positive definite";
         return MSTOPO_NOT_SPD;
       }
-    // the CUDA-core patch solves stream the packed blocks (FP64 always, FP32 unless the tensor
-    // cores take the FP32 patch solves)
-    // The tensor-core kernel's line has a fixed MMA chain (68 tcgen05.mma whatever the number
-    // of columns) and streams its own factor format; it pays off only with many full
-    // 16-column groups per SM.  Measured (MIXED solves, all realisations): 2048x1024, 42
-    // patches per SM: CUDA cores 220 ms, tensor cores 275 ms; 3200x4096, 257 per SM: CUDA
-    // cores 603 ms, tensor cores 557 ms.  The switch sits between the two.
-    pc.patch_tc = h->patch_tc > 0 || (h->patch_tc < 0 && (long long)pc.Nc * nsv >= 128LL * sms);
+    // The patch solves stream the packed blocks: FP64 always; FP32 on the CUDA cores or, for
+    // H = 8, 16, 32, on the tensor cores (csrc/patch_twtc.cu: 128 patches of a type per MMA,
+    // its own pack made from the FP64 one).  The tensor-core kernel runs one cluster of two
+    // CTAs per group and one CTA per SM, and a line step is a fixed MMA chain whatever the
+    // number of patches, so it pays off with many patches per type.  Measured (FP32 patch
+    // solves of realisation 0, one launch):
+    //   1024x512 (561 patches, 25 types): CUDA cores 0.26 ms, tensor cores 0.59 ms;
+    //   2048x1024 (2,145 patches, 165 types): 0.77 ms, 1.72 ms;
+    //   3200x4096 (13,029 patches, 25 types): 3.51 ms, 1.24 ms.
+    // Cost model from these: a tensor-core wave (up to one CTA per SM) takes 2.3 times an
+    // R = 4 CUDA-core wave; the automatic choice takes the cheaper.
+    const bool tw_ok = patch_twtc_ok(nbP);
+    if (h->patch_tc > 0 && !tw_ok) {
+      h->err = "tensor-core patch solves need H = 8, 16 or 32";
+      return MSTOPO_INVALID_ARG;
+    }
+    const double tw_waves = 2.3 * (double)((2 * tw_groups + std::max(sms, 1) - 1) / std::max(sms, 1));
+    pc.patch_tc = tw_ok && (h->patch_tc > 0 || (h->patch_tc < 0 && tw_waves < tri_waves));
     const size_t tl = (size_t)TP * patch_tri_system_elems(nbP, NP);
     CKB(cudaMalloc(&pc.d_tri64, tl * 8));
     if (!pc.patch_tc) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
@@ -1269,19 +1262,9 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     cudaFree(dAr); cudaFree(dBr); cudaFree(dLr); cudaFree(dCr); cudaFree(dSr); cudaFree(dLm);
     cudaFree(dfr); cudaFree(d_st2);
     if (pc.patch_tc) {
-      // tensor-core FP32 line pack: [Linv_k | -W_k], [Linv_k^T | -V_k]
-      const double* pCc = dC + (size_t)T * (NA - 1) * nnA;
-      double *dW, *dV;
-      CKB(cudaMalloc(&dW, (size_t)TP * NP * nnP * 8));
-      CKB(cudaMalloc(&dV, (size_t)TP * NP * nnP * 8));
-      note_launch(), k_patch_wv<<<dim3(TP, NP, 2), PC_THREADS, 0, s>>>(pLi, pCc, dW, dV, nbP, NP);
-      CKB(cudaGetLastError());
-      pc.tc_line_bytes = patch_tc_line_bytes(nbP);
-      CKB(cudaMalloc(&pc.d_ptc, (size_t)TP * 2 * NP * pc.tc_line_bytes));
-      CKB(patch_tc_pack(pLi, dW, dV, TP, nbP, NP, pc.d_ptc, s));
-      CKB(cudaStreamSynchronize(s));
-      cudaFree(dW);
-      cudaFree(dV);
+      const TwGeom tw = patch_twtc_geometry(nbP, NP);
+      CKB(cudaMalloc(&pc.d_ptw, (size_t)TP * tw.SS));
+      CKB(patch_twtc_pack(pc.d_tri64, TP, nbP, NP, pc.d_ptw, s));
     }
     CKB(cudaStreamSynchronize(s));
   }
@@ -1458,11 +1441,14 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   };
   CKB(cudaStreamSynchronize(s));
   if (!sgs) CKB(build_groups(pc.pg[0], P));
-  if (!sgs && pc.patch_tc) CKB(build_groups(pc.pg[1], PATCH_COLS));
+  if (!sgs && pc.patch_tc) CKB(build_groups(pc.pg[1], TW_M));
   if (!sgs) CKB(build_groups(pc.pg[2], std::min(P, PATCH_COLS_F64)));
+  if (pc.d_ptw) CKB(cudaMalloc(&pc.d_twu, (size_t)pc.pg[1].n * 2 * TW_M * nbP * 4));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
   CKB(cudaMalloc(&pc.d_uc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
-  const size_t xg = (size_t)std::max({pc.pg[0].n, pc.pg[1].n, pc.pg[2].n}) * nP * PATCH_COLS;
+  // work buffer of the patch results: [group][NL][columns][nbP] for the largest group set
+  const size_t xg = std::max({(size_t)pc.pg[0].n * PATCH_COLS, (size_t)pc.pg[2].n * PATCH_COLS,
+                              (size_t)pc.pg[1].n * TW_M}) * nP;
   if (xg) {
     CKB(cudaMalloc(&pc.d_zp32, xg * 4));
     CKB(cudaMalloc(&pc.d_zp64, xg * 8));
@@ -1545,12 +1531,12 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
   const PatchGroups& G = pc.pg[sizeof(T) == 8 ? 2 : (use_tc ? 1 : 0)];
   int Rcols = 4;
   if (part != 1) {
-    const int Q = (G.P + 3) / 4;
-    Rcols = use_tc ? 4 * Q : patch_tri_cols(G.P);
+    Rcols = use_tc ? TW_M : patch_tri_cols(G.P);
     cudaEvent_t pa = prof_begin(h->prof, s);
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-      e = use_tc ? patch_tc_solve(h, Q, r, sys0, nsys, Xg) : patch_tri_solve_f32(h, G, r, sys0, nsys, Xg);
+      e = use_tc ? patch_twtc_solve(h, G, r, sys0, nsys, Xg, pc.d_twu)
+                 : patch_tri_solve_f32(h, G, r, sys0, nsys, Xg);
     } else {
       e = patch_tri_solve_f64(h, G, r, sys0, nsys, Xg);
     }
@@ -1568,7 +1554,7 @@ static cudaError_t apply_impl(mstopo_handle* h, const T* r, T* z, int sys0, int 
   note_launch(), k_combine<T><<<dim3(cdiv(h->nelx + 1, 128), h->nely + 1, nsys), 128, 0, s>>>(z, n, sys0, pc.Nc, h->nelx, h->nely, pc.H, pc.ncx, pc.ncy,
                                                pc.d_type_of_agg, pc.d_kept, pc.d_coff, psi, pc.kmax,
                                                pc.d_uc, pc.Nt, G.d_agg, G.d_agg + (size_t)pc.nsv * pc.Nc, Xg,
-                                               Rcols, h->d_nmask, part);
+                                               Rcols, use_tc ? 1 : 0, h->d_nmask, part);
   return cudaGetLastError();
 }
 

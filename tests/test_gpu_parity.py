@@ -104,19 +104,19 @@ def test_patch_solves_match_sparse_lu():
 
 
 @pytest.mark.parametrize("size,H,etas", [
-    ((128, 64), 32, (0.5,)),             # nb = 130: factor rows 128, 129 on the CUDA cores
-    ((40, 24), 4, (0.5,)),               # 4 columns per CTA, one patch each
-    ((60, 40), 2, (0.5,)),               # 8 columns
-    ((80, 64), 2, (0.5,)),               # 12 columns
-    ((128, 128), 2, (0.5,)),             # 16 columns
-    ((1024, 768), 32, (0.3, 0.5, 0.7)),  # 16 columns of 130-row lines, three realisations
+    ((128, 64), 32, (0.5,)),             # nb = 130: 17 K-steps, N = 144, partial groups
+    ((256, 128), 16, (0.5,)),            # nb = 66: 9 K-steps
+    ((192, 96), 8, (0.3, 0.5, 0.7)),     # nb = 34: 5 K-steps, three realisations
+    ((1024, 768), 32, (0.3, 0.5, 0.7)),  # 825 patches per realisation: several full groups
 ])
 def test_tensor_core_patch_solves(size, H, etas):
-    """The FP32 patch solves on the tensor cores against the FP64 patch solves of the same
-    factors (Sec. 3.2), next to the FP32 CUDA-core solves.  A TF32 pair (high + low part)
-    carries 22 significant bits where FP32 carries 24, for the factor and for the vectors, so
-    the bound is the FP32 error scaled by that representation (4x each) plus 2^-22-relative
-    slack; both must stay far below the preconditioner's own approximation error."""
+    """The FP32 patch solves on the tensor cores (up to 128 patches of one type as the MMA's
+    rows, the two-sided elimination of Sec. 3.2) against the FP64 patch solves of the same
+    factors, next to the FP32 CUDA-core solves; both must stay far below the preconditioner's
+    own approximation error.  Every line product sums 3 KS tensor-core MMAs (KS = ceil(nb / 8)
+    K-steps, TF32 high and low parts of both operands) in one FP32 accumulator, each of which
+    may drop up to one FP32 unit of the running sum, so the bound is 3 KS 2^-23 on top of four
+    times the CUDA-core FP32 error."""
     m = _gpu()
     wl = workloads.small(*size, seed=21, kind="voids", H=H, n_eig=4, etas=etas, Emin=1e-3)
     rng = np.random.default_rng(5)
@@ -132,8 +132,25 @@ def test_tensor_core_patch_solves(size, H, etas):
         assert torch.isfinite(z32).all()
         err[tc] = (torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)).item()
         del prob
+    print(f"tensor-core patch solves {size} H={H}: rel. error {err['1']:.3e} "
+          f"(CUDA-core FP32 {err['0']:.3e})")
     assert err["1"] < 1e-5, err
-    assert err["1"] <= 16.0 * err["0"] + 2.0 ** -22, err
+    ks = (2 * (2 * H + 1) + 7) // 8
+    assert err["1"] <= 3 * ks * 2.0 ** -23 + 4.0 * err["0"], err
+
+
+def test_tensor_core_patch_solves_reject_other_line_sizes():
+    """The tensor-core kernel is compiled for H = 8, 16 and 32; forcing it with another H is an
+    invalid argument, while the automatic choice falls back to the CUDA cores."""
+    m = _gpu()
+    wl = workloads.small(40, 24, seed=21, kind="voids", H=4, n_eig=4)
+    prob = make_problem(m, wl, precision="mixed", patch_kernel="tensor_cores")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    with pytest.raises(m.MstopoError, match="H = 8, 16 or 32"):
+        prob.build_preconditioner()
+    prob = make_problem(m, wl, precision="mixed", patch_kernel="auto")
+    prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+    prob.build_preconditioner()
 
 
 def test_eigenpairs_satisfy_generalised_eigenproblem():
@@ -296,8 +313,8 @@ def test_solve_with_blocktri_coarse_solver(precision):
 @pytest.mark.parametrize("H", [8, 32])
 def test_mixed_solve_with_tensor_core_patches(H):
     """The mixed flexible CG with its FP32 patch solves forced onto the tensor cores (H = 32:
-    130-row lines, factor rows 128 and 129 on the CUDA cores) converges to the same solution
-    as sparse LU, three realisations."""
+    130-DOF lines, N = 144 per MMA) converges to the same solution as sparse LU, three
+    realisations."""
     m = _gpu()
     wl = workloads.small(128, 64, seed=23, kind="voids", H=H, n_eig=6, etas=(0.3, 0.5, 0.7),
                          rmin=2.0, beta=8.0)
