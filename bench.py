@@ -211,10 +211,13 @@ def run_ours(args, rank: int, world: int):
     rho = torch.from_numpy(wl.rho).to(dev)
     f = torch.from_numpy(wl.force).to(dev)
 
+    # the FP32 patch-solve configuration is autotuned: the first (warm-up) build times each
+    # candidate, the timed steps keep the choice
     def problem(prec, preconditioner="additive", krylov="fcg"):
         return m.Problem(wl.nelx, wl.nely, wl.fixed, nu=wl.nu, E0=wl.E0, Emin=wl.Emin,
                          penal=wl.penal, H=wl.H, n_eig=wl.n_eig, precision=prec, tol=wl.tol,
-                         max_iter=5000, preconditioner=preconditioner, krylov=krylov)
+                         max_iter=5000, preconditioner=preconditioner, krylov=krylov,
+                         autotune=not args.no_autotune)
 
     mixed, fp64 = problem("mixed"), problem("fp64")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -365,11 +368,13 @@ def run_ours(args, rank: int, world: int):
     # headline: the flexible CG's own launch (all three realisations in one launch, inputs zero
     # at the Dirichlet DOFs); beside it the single-vector ABI call that reads the input mask
     mv = None
+    pt5 = None
     if not args.skip_big_matvec:
         import numpy as np
         big = workloads.make("mbb_c5")
         pb = m.Problem(big.nelx, big.nely, big.fixed, nu=big.nu, E0=big.E0, Emin=big.Emin,
-                       penal=big.penal, H=big.H, n_eig=big.n_eig, precision="mixed")
+                       penal=big.penal, H=big.H, n_eig=big.n_eig, precision="mixed",
+                       autotune=not args.no_autotune)
         pb.set_design(torch.from_numpy(big.rho).to(dev), big.rmin, big.beta, big.etas, big.cell)
         ns = len(big.etas)
         nb_nodes = (big.nelx + 1) * (big.nely + 1)
@@ -403,8 +408,46 @@ def run_ours(args, rank: int, world: int):
               "bytes_per_node": "u 8 + y 8 (float2) + E 4/element per system, output mask 1 once per launch",
               "single_vector_masked_input": {"avg_launch_ms": t_one, "algorithmic_bytes": byts + 2 * mask_b,
                                              "gbs": gbs1, "frac": gbs1 / peaks["hbm_gbs"]}}
-        pb.close()
         del u32, y32
+
+        # ---- FP32 patch solves on the same workload (realisation 0, one launch) with the
+        #      kernel the automatic choice builds (the tensor cores here: 128 patches of a
+        #      type per MMA, profiles/k_patch_twtc_mbb_c5_800x1024.md) ----
+        bi5 = pb.build_preconditioner(-1)
+        r5 = torch.randn((big.nely + 1, big.nelx + 1, 2), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            pb.apply_precond(r5, m.MIXED, 2)
+        pb.set_profiling(True)
+        for _ in range(10):
+            flush.zero_()
+            pb.apply_precond(r5, m.MIXED, 2)
+        sp = pb.stats()
+        pb.set_profiling(False)
+        t_p5 = sp["patch_solve"]["ms"] / max(sp["patch_solve"]["launches"], 1)
+        nl5 = 2 * big.H + 1
+        nb5 = 2 * nl5
+        alg5 = 4.0 * nl5 * nb5 * nb5 * bi5["n_agglomerates"]       # 4 n b flops per patch solve
+        tc5 = bi5["patch_kernel"] == 2
+        groups5 = bi5["patch_groups"] // ns                          # realisation 0's groups
+        ks5, npad5 = (nb5 + 7) // 8, (nb5 + 15) // 16 * 16
+        # executed on the tensor cores: per group two CTAs x NL line steps x 3 KS MMAs of
+        # 128 x npad x 8
+        mma5 = 2.0 * groups5 * nl5 * 3 * ks5 * 2 * 128 * npad5 * 8
+        tf32_peak = peaks["bf16_tflops"] / 2.0   # TF32 at half the BF16 rate (nominal ratio)
+        pt5 = {
+            "kernel": "k_patch_twtc<130> (tensor cores)" if tc5 else "k_patch_tri<float> (CUDA cores)",
+            "choice": {0: "cost model", 1: "autotuned", 2: "autotuned earlier"}[bi5["patch_tuned"]],
+            "cols": bi5["patch_cols"], "realisation": 0, "patches": bi5["n_agglomerates"],
+            "types": bi5["n_types"], "groups": groups5, "avg_launch_ms": t_p5,
+            "algorithmic_gflop": alg5 / 1e9,
+            "fp32_equivalent_tflops": alg5 / (t_p5 * 1e-3) / 1e12,
+            "frac_of_fp32_peak": alg5 / (t_p5 * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+            "tf32_mma_tflops": (mma5 / (t_p5 * 1e-3) / 1e12) if tc5 else None,
+            "tf32_peak_tflops": tf32_peak if tc5 else None,
+            "frac_of_tf32_peak": (mma5 / (t_p5 * 1e-3) / 1e12 / tf32_peak) if tc5 else None,
+            "peak_source": "FP32: derived (152 SMs x 128 FMA/clk x 2 x 2070 MHz); TF32: measured "
+                           "BF16 peak x the nominal TF32/BF16 ratio 1/2"}
+        pb.close()
 
     # ---- e2e through the host-pointer entry point (pinned buffers, copies timed) ----
     fh = torch.from_numpy(wl.force).pin_memory()
@@ -453,7 +496,7 @@ def run_ours(args, rank: int, world: int):
                   "phases_ms": {k: statistics.mean(p[k] for p in per)
                                 for k in ("design", "build", "solve", "sens")},
                   "build": binfo},
-        "matvec": mv, "roofline": roofline, "kernels": shares, "gpu_launches": launches,
+        "matvec": mv, "patch_solve_26m": pt5, "roofline": roofline, "kernels": shares, "gpu_launches": launches,
         "clocks": clocks, "e2e": e2e, "wall_s_timed": t_wall, "peaks": peaks,
     }
     if not args.skip_cpu:
@@ -758,6 +801,8 @@ def main():
                     help="run the whole path on a named workload (mbb_c1, mbb_c2, mbb_c3, mbb_c5, "
                          "cantilever_batch) and print one JSON line (no benchmark)")
     ap.add_argument("--workload-mixed-only", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="choose the FP32 patch-solve configuration by the cost model instead of timing")
     ap.add_argument("--patch-kernel", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
                     help="with --workload-run: the FP32 patch-solve kernel")
     ap.add_argument("--design-loop", default=None,

@@ -94,6 +94,13 @@ typedef enum {
 #define MSTOPO_EXEC_NO_GRAPHS 1       /* run every flexible-CG iteration as direct launches      */
 #define MSTOPO_EXEC_NO_SIDE_STREAM 2  /* run the preconditioner's coarse chain on the main stream
                                          instead of a side stream beside the patch solves        */
+#define MSTOPO_EXEC_AUTOTUNE 4        /* with MSTOPO_PATCH_AUTO: the first build of a problem shape
+                                         times every FP32 patch-solve configuration (CUDA cores
+                                         with 4, 8 and 16 columns per group; the tensor cores
+                                         where compiled) and the process keeps the fastest for
+                                         that shape; without it a measured cost model chooses.
+                                         The chosen kernel fixes the FP32 rounding, so two
+                                         processes may differ in the last bits.                */
 
 typedef enum {
   MSTOPO_FIELD_RHO_TILDE = 0,  /* filtered design (design layout)                         */
@@ -146,6 +153,13 @@ typedef struct {
   int32_t coarse_solver;      /* MSTOPO_COARSE_DENSE or MSTOPO_COARSE_BLOCKTRI, as built   */
   int32_t coarse_line;        /* unknowns per coarse line (block size of K_c)               */
   int32_t coarse_lines;       /* number of coarse lines (blocks of K_c)                     */
+  int32_t patch_kernel;       /* FP32 patch solves as built: MSTOPO_PATCH_CUDA_CORES or
+                                 MSTOPO_PATCH_TENSOR_CORES (0: no patch solves, SGS)        */
+  int32_t patch_groups;       /* their work groups over all realisations (patches of one
+                                 type and realisation each; 128 per tensor-core group)      */
+  int32_t patch_cols;         /* patches per group: 4, 8, 16 (CUDA cores) or 128            */
+  int32_t patch_tuned;        /* 0: cost model, 1: timed in this build (MSTOPO_EXEC_AUTOTUNE),
+                                 2: the choice kept from an earlier build of the same shape */
 } mstopo_build_info;
 
 typedef struct {

@@ -93,7 +93,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
             (d->preconditioner == MSTOPO_PREC_ADDITIVE ||
              d->preconditioner == MSTOPO_PREC_MULTIPLICATIVE_SGS) &&
             d->patch_kernel >= MSTOPO_PATCH_AUTO && d->patch_kernel <= MSTOPO_PATCH_TENSOR_CORES &&
-            (d->exec_flags & ~(MSTOPO_EXEC_NO_GRAPHS | MSTOPO_EXEC_NO_SIDE_STREAM)) == 0 &&
+            (d->exec_flags & ~(MSTOPO_EXEC_NO_GRAPHS | MSTOPO_EXEC_NO_SIDE_STREAM | MSTOPO_EXEC_AUTOTUNE)) == 0 &&
             (d->krylov == MSTOPO_KRYLOV_FCG || d->krylov == MSTOPO_KRYLOV_GMRES) &&
             d->gmres_restart >= 0 && d->gmres_restart <= 200;
   if (!ok) {
@@ -118,6 +118,7 @@ mstopo_status mstopo_create(const mstopo_problem* d, mstopo_handle** out) {
     return fail(MSTOPO_CUDA_ERROR);
   }
   if (d->exec_flags & MSTOPO_EXEC_NO_GRAPHS) h->graphs_enabled = 0;
+  if (d->exec_flags & MSTOPO_EXEC_AUTOTUNE) h->autotune = 1;
   h->patch_tc = d->patch_kernel == MSTOPO_PATCH_AUTO ? -1 : (d->patch_kernel == MSTOPO_PATCH_TENSOR_CORES ? 1 : 0);
   if (d->exec_flags & MSTOPO_EXEC_NO_SIDE_STREAM) {
     cudaStreamDestroy(h->s_side);

@@ -256,6 +256,7 @@ struct mstopo_handle {
   int loop_graph_failed = 0;          // the device-side solve loop could not be built: host loop
   long long device_loop_solves = 0;   // solves that ran the device-side loop
   int patch_tc = -1;                  // FP32 patch solves on the tensor cores: -1 by problem size, 0 off, 1 on
+  int autotune = 0;                   // MSTOPO_EXEC_AUTOTUNE: time the patch-solve configurations
   int inject = 0;                     // test injection (mstopo_inject), consumed by its target
   long long builds = 0;               // preconditioner builds (explicit and automatic)
   int base_iters = -1;                // iterations of the first solve after the last build

@@ -29,6 +29,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
 
 #include <cooperative_groups.h>
@@ -946,6 +948,20 @@ __global__ void __launch_bounds__(256) k_combine(
 }
 
 // ------------------------------------------------------------------------------ host side
+// Patch-solve configurations chosen by timing (MSTOPO_EXEC_AUTOTUNE), kept per problem shape
+// for the process: (DOFs per patch line, lines, agglomerates, types, realisations) ->
+// (tensor cores, patches per group).
+namespace {
+struct TuneKey {
+  int nb, nl, nc, nt, ns;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nb, nl, nc, nt, ns) < std::tie(o.nb, o.nl, o.nc, o.nt, o.ns);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+}  // namespace
+
 #define CKB(x)                                                                  \
   do {                                                                          \
     cudaError_t e_ = (x);                                                       \
@@ -1195,6 +1211,23 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     for (int t = 0; t < T; ++t) tw_groups += (per_type[t] + TW_M - 1) / TW_M;
     tw_groups *= nsv;
   }
+  // autotuning: a shape timed before keeps its choice; otherwise every candidate is built and
+  // timed after the work groups (step 5)
+  const bool tune = !sgs && h->autotune && h->patch_tc < 0;
+  const TuneKey tkey{nbP, NP, pc.Nc, T, nsv};
+  int tuned = 0;              // 0 cost model, 1 timed now, 2 kept
+  int tuned_tc = -1;
+  if (tune) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tkey);
+    if (it != g_tune.end()) {
+      tuned = 2;
+      tuned_tc = it->second.first;
+      P = it->second.second == TW_M ? P : it->second.second;
+    } else {
+      tuned = 1;
+    }
+  }
   if (!patch_tri_assignment_ok(nbP)) {
     h->err = "H > 32 is not supported by the patch solve";
     return MSTOPO_INVALID_ARG;
@@ -1254,14 +1287,17 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     }
     const double tw_waves = 2.3 * (double)((2 * tw_groups + std::max(sms, 1) - 1) / std::max(sms, 1));
     pc.patch_tc = tw_ok && (h->patch_tc > 0 || (h->patch_tc < 0 && tw_waves < tri_waves));
+    if (tuned == 2) pc.patch_tc = tuned_tc;
     const size_t tl = (size_t)TP * patch_tri_system_elems(nbP, NP);
     CKB(cudaMalloc(&pc.d_tri64, tl * 8));
-    if (!pc.patch_tc) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
+    // timing needs every candidate's pack: the FP32 CUDA-core one and, where compiled, the
+    // tensor-core one
+    if (!pc.patch_tc || tuned == 1) CKB(cudaMalloc(&pc.d_tri32, tl * 4));
     CKB(patch_tri_pack(pLi, pB, dLr, dBr, dLm, TP, nbP, NP, NLr, pc.d_tri64, pc.d_tri32, s));
     CKB(cudaStreamSynchronize(s));
     cudaFree(dAr); cudaFree(dBr); cudaFree(dLr); cudaFree(dCr); cudaFree(dSr); cudaFree(dLm);
     cudaFree(dfr); cudaFree(d_st2);
-    if (pc.patch_tc) {
+    if (pc.patch_tc || (tuned == 1 && tw_ok)) {
       const TwGeom tw = patch_twtc_geometry(nbP, NP);
       CKB(cudaMalloc(&pc.d_ptw, (size_t)TP * tw.SS));
       CKB(patch_twtc_pack(pc.d_tri64, TP, nbP, NP, pc.d_ptw, s));
@@ -1441,7 +1477,7 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   };
   CKB(cudaStreamSynchronize(s));
   if (!sgs) CKB(build_groups(pc.pg[0], P));
-  if (!sgs && pc.patch_tc) CKB(build_groups(pc.pg[1], TW_M));
+  if (!sgs && (pc.patch_tc || pc.d_ptw)) CKB(build_groups(pc.pg[1], TW_M));
   if (!sgs) CKB(build_groups(pc.pg[2], std::min(P, PATCH_COLS_F64)));
   if (pc.d_ptw) CKB(cudaMalloc(&pc.d_twu, (size_t)pc.pg[1].n * 2 * TW_M * nbP * 4));
   CKB(cudaMalloc(&pc.d_rc, (size_t)MSTOPO_MAX_SYS * Nt * 8));
@@ -1452,6 +1488,74 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   if (xg) {
     CKB(cudaMalloc(&pc.d_zp32, xg * 4));
     CKB(cudaMalloc(&pc.d_zp64, xg * 8));
+  }
+  if (tuned == 1) {
+    // time one launch of every candidate (after one untimed launch) on a zero input: the
+    // kernels' time does not depend on the values
+    float* r0 = nullptr;
+    CKB(cudaMalloc(&r0, (size_t)nsv * h->n_dof * sizeof(float)));
+    CKB(cudaMemsetAsync(r0, 0, (size_t)nsv * h->n_dof * sizeof(float), s));
+    cudaEvent_t t0, t1;
+    CKB(cudaEventCreate(&t0));
+    CKB(cudaEventCreate(&t1));
+    float best_ms = 0.f;
+    int best_tc = 0, best_p = P;
+    const int cand[4] = {4, 8, 16, TW_M};
+    for (int ci = 0; ci < 4; ++ci) {
+      const bool tc = cand[ci] == TW_M;
+      if (tc && !pc.d_ptw) continue;
+      PatchGroups Gt;
+      const PatchGroups* G = &pc.pg[tc ? 1 : 0];
+      if (!tc && cand[ci] != P) {
+        CKB(build_groups(Gt, cand[ci]));
+        G = &Gt;
+      }
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CKB(cudaEventRecord(t0, s));
+        CKB(tc ? patch_twtc_solve(h, *G, r0, 0, nsv, pc.d_zp32, pc.d_twu)
+               : patch_tri_solve_f32(h, *G, r0, 0, nsv, pc.d_zp32));
+        CKB(cudaEventRecord(t1, s));
+        CKB(cudaEventSynchronize(t1));
+        CKB(cudaEventElapsedTime(&ms, t0, t1));
+      }
+      if (G == &Gt) {
+        cudaFree(Gt.d_perm); cudaFree(Gt.d_type); cudaFree(Gt.d_first); cudaFree(Gt.d_count);
+        cudaFree(Gt.d_sys); cudaFree(Gt.d_agg);
+      }
+      if (ci == 0 || ms < best_ms) {
+        best_ms = ms;
+        best_tc = tc ? 1 : 0;
+        best_p = cand[ci];
+      }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFree(r0);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[tkey] = {best_tc, best_p};
+    }
+    // keep the winner's pack and groups only
+    pc.patch_tc = best_tc;
+    if (best_tc) {
+      dfree(pc.d_tri32);
+      pc.d_tri32 = nullptr;
+    } else {
+      PatchGroups& G1 = pc.pg[1];
+      dfree(G1.d_perm); dfree(G1.d_type); dfree(G1.d_first); dfree(G1.d_count); dfree(G1.d_sys); dfree(G1.d_agg);
+      G1 = PatchGroups();
+      dfree(pc.d_ptw); dfree(pc.d_twu);
+      pc.d_ptw = nullptr;
+      pc.d_twu = nullptr;
+      if (best_p != P) {
+        PatchGroups& G0 = pc.pg[0];
+        dfree(G0.d_perm); dfree(G0.d_type); dfree(G0.d_first); dfree(G0.d_count); dfree(G0.d_sys); dfree(G0.d_agg);
+        G0 = PatchGroups();
+        P = best_p;
+        CKB(build_groups(G0, P));
+      }
+    }
   }
   CKB(cudaEventRecord(ev[5], s));
   // build report
@@ -1467,6 +1571,10 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
     info->coarse_solver = pc.coarse_mode;
     info->coarse_line = pc.nbc;
     info->coarse_lines = pc.NLc;
+    info->patch_kernel = sgs ? 0 : (pc.patch_tc ? MSTOPO_PATCH_TENSOR_CORES : MSTOPO_PATCH_CUDA_CORES);
+    info->patch_groups = sgs ? 0 : pc.pg[pc.patch_tc ? 1 : 0].n;
+    info->patch_cols = sgs ? 0 : (pc.patch_tc ? TW_M : pc.pg[0].P);
+    info->patch_tuned = tuned;
     info->eig_sweeps = *std::max_element(esw.begin(), esw.end());
     info->eig_residual = *std::max_element(eres.begin(), eres.end());
     cudaEventElapsedTime(&info->ms_hash, ev[0], ev[1]);

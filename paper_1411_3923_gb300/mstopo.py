@@ -45,7 +45,9 @@ class _BuildInfo(C.Structure):
                 ("eig_sweeps", C.c_int32), ("eig_residual", C.c_double), ("ms_hash", C.c_float),
                 ("ms_eigen", C.c_float), ("ms_patch_factor", C.c_float), ("ms_coarse", C.c_float),
                 ("ms_total", C.c_float), ("coarse_solver", C.c_int32),
-                ("coarse_line", C.c_int32), ("coarse_lines", C.c_int32)]
+                ("coarse_line", C.c_int32), ("coarse_lines", C.c_int32),
+                ("patch_kernel", C.c_int32), ("patch_groups", C.c_int32),
+                ("patch_cols", C.c_int32), ("patch_tuned", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -58,7 +60,7 @@ class _Stats(C.Structure):
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
 PRECONDITIONERS = {"additive": 0, "sgs": 1}   # mstopo_preconditioner
 PATCH_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}   # mstopo_patch_kernel
-EXEC_NO_GRAPHS, EXEC_NO_SIDE_STREAM = 1, 2   # mstopo_problem.exec_flags bits
+EXEC_NO_GRAPHS, EXEC_NO_SIDE_STREAM, EXEC_AUTOTUNE = 1, 2, 4   # mstopo_problem.exec_flags bits
 KRYLOV = {"fcg": 0, "gmres": 1}   # mstopo_krylov
 
 KERNEL_IDS = {"patch_solve": 0, "matvec_f32": 1, "matvec_f64": 2, "coarse_solve": 3}
@@ -186,7 +188,9 @@ class Problem:
     ``precision``: "mixed" (FP64 outer solve, FP32 inner arithmetic) or "fp64".
     ``patch_kernel``: "auto", "cuda_cores" or "tensor_cores" for the FP32 patch solves.
     ``graphs`` / ``side_stream``: False runs the flexible CG without CUDA graphs / the
-    preconditioner's coarse chain on the main stream."""
+    preconditioner's coarse chain on the main stream.
+    ``autotune``: with patch_kernel "auto", the first build of a problem shape times every FP32
+    patch-solve configuration and the process keeps the fastest (MSTOPO_EXEC_AUTOTUNE)."""
 
     def __init__(self, nelx: int, nely: int, fixed: np.ndarray, *, nu: float = 0.3,
                  E0: float = 1.0, Emin: float = 1e-9, penal: float = 3.0, H: int = 16,
@@ -196,7 +200,7 @@ class Problem:
                  reuse_preconditioner: bool = False, rebuild_ratio: float = 0.0,
                  preconditioner: str = "additive", patch_kernel: str = "auto",
                  graphs: bool = True, side_stream: bool = True, krylov: str = "fcg",
-                 gmres_restart: int = 0):
+                 gmres_restart: int = 0, autotune: bool = False):
         lib = load()
         self.nelx, self.nely = nelx, nely
         self._fixed = np.ascontiguousarray(fixed, dtype=np.uint8).reshape(-1)
@@ -206,7 +210,8 @@ class Problem:
                      local_shift, stream, COARSE_SOLVERS[coarse_solver],
                      1 if reuse_preconditioner else 0, rebuild_ratio,
                      PRECONDITIONERS[preconditioner], PATCH_KERNELS[patch_kernel],
-                     (0 if graphs else EXEC_NO_GRAPHS) | (0 if side_stream else EXEC_NO_SIDE_STREAM),
+                     (0 if graphs else EXEC_NO_GRAPHS) | (0 if side_stream else EXEC_NO_SIDE_STREAM)
+                     | (EXEC_AUTOTUNE if autotune else 0),
                      KRYLOV[krylov], gmres_restart)
         h = C.c_void_p()
         st = lib.mstopo_create(C.byref(d), C.byref(h))

@@ -673,3 +673,38 @@ def test_gmres_with_multiplicative_sgs_matches_oracle(precision, etas):
     print("GPU", [i["iterations"] for i in infos], "oracle", it_ref, rel_ref)
     assert rel_ref <= 1e-10
     assert abs(infos[k0]["iterations"] - it_ref) <= max(2, 0.05 * it_ref)
+
+
+def test_autotuned_patch_solves_time_every_configuration_once_per_shape():
+    """MSTOPO_EXEC_AUTOTUNE: the first build of a shape times the FP32 patch-solve
+    configurations and reports it (patch_tuned 1); a second problem of the same shape keeps
+    the choice (2) and builds the same kernel; the solves match sparse LU as with the cost
+    model's choice, and the patch solves match the FP64 ones within the FP32 bound of
+    whichever kernel was chosen."""
+    m = _gpu()
+    wl = workloads.small(256, 128, seed=31, kind="voids", H=32, n_eig=4, etas=(0.5,),
+                         rmin=2.0, beta=8.0)
+    infos = []
+    for _ in range(2):
+        prob = make_problem(m, wl, "mixed", tol=1e-10, autotune=True)
+        prob.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
+        infos.append(prob.build_preconditioner())
+        u, sinfo = prob.solve(cuda(wl.force), -1)
+        assert sinfo[0]["status"] == 0 and sinfo[0]["rel_residual"] <= 1e-10
+        r = cuda(np.random.default_rng(3).standard_normal((wl.nely + 1, wl.nelx + 1, 2)))
+        z64 = prob.apply_precond(r, m.FP64, 2)
+        z32 = prob.apply_precond(r, m.MIXED, 2)
+        err = (torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)).item()
+        assert err < 1e-5, (infos[-1], err)
+        del prob
+    a, b = infos
+    assert (a["patch_tuned"], b["patch_tuned"]) in ((1, 2), (2, 2))   # (2, 2) if an earlier test timed it
+    assert a["patch_kernel"] == b["patch_kernel"] and a["patch_cols"] == b["patch_cols"]
+    assert a["patch_cols"] in (4, 8, 16, 128)
+    assert (a["patch_kernel"] == 2) == (a["patch_cols"] == 128)
+    ref = pipeline.run(wl, "direct", with_grad=False)
+    grid, K0, oprob, _ = pipeline.build(wl)
+    Kf = oprob.free_matrix(ref["E"][0])
+    ug = grid.nodal_from_neutral(u[0].cpu().numpy())[oprob.free]
+    ur = grid.nodal_from_neutral(ref["u"][0])[oprob.free]
+    assert_energy(Kf, ur, ug)

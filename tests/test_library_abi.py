@@ -95,7 +95,7 @@ def test_unknown_preconditioner_kind_is_rejected():
         assert h.value is None
 
 
-@pytest.mark.parametrize("patch_kernel,exec_flags", [(3, 0), (-1, 0), (0, 4), (0, -1)])
+@pytest.mark.parametrize("patch_kernel,exec_flags", [(3, 0), (-1, 0), (0, 8), (0, -1)])
 def test_unknown_patch_kernel_or_exec_flag_is_rejected(patch_kernel, exec_flags):
     """The kernel-path switches are problem fields and are validated before any GPU work."""
     import ctypes
