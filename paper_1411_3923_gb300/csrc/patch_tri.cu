@@ -271,7 +271,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
     const int* __restrict__ perm, const uint8_t* __restrict__ pfree, const T* __restrict__ pack,
     TriGeom geo, T* __restrict__ Xg, int* __restrict__ err) {
   using V2 = typename Pair<T>::type;
-  __shared__ __align__(8) uint64_t bars[NBUF];
+  // one stage (NBUF = 1): the block is split into its symmetric inverse (one buffer, refilled
+  // as soon as the product that reads it is done) and its coupling (two buffers, filled a
+  // step ahead), so that neither copy waits at the top of a step; bars[0] the inverse,
+  // bars[1], bars[2] the couplings.  Two stages: a ring of whole blocks.
+  constexpr bool SPLIT = NBUF == 1;
+  __shared__ __align__(8) uint64_t bars[NBUF + 2];
   __shared__ int s_abort;
   __shared__ int s_ox[16], s_oy[16];          // lower-left node of each patch's box
   __shared__ int s_rowoff[160];               // offset of every factor row in a block
@@ -291,8 +296,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
   T* X = Xg + (long long)grp * NL * R * nb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  T* ring = reinterpret_cast<T*>(smraw);                  // [NBUF][LBM]
-  T* vt = ring + (long long)NBUF * geo.LBM;               // [R][NV] input t of the product
+  T* ring = reinterpret_cast<T*>(smraw);                  // [NBUF][LBM], or [TB] when split
+  T* cbuf = ring + geo.TB;                                // split: [2][12 nb] couplings
+  T* vt = ring + (SPLIT ? (long long)geo.TB + 24LL * nb : (long long)NBUF * geo.LBM);   // [R][NV] input t
   T* vy = vt + NV * R;                                    // [R][NV] its result S^-1 t
   T* vw = vy + NV * R;                                    // [R][NV] x of the current line
   T* vp = vw + NV * R;                                    // [R][NV] w of the previous line
@@ -312,7 +318,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
   for (int q = tid; q < nb; q += NTH) s_rowoff[q] = tri_rowoff(geo, q);
   if (tid == 0) {
     s_abort = 0;
-    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; b < NBUF + 2; ++b) mbar_init(&bars[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero the vectors (rows nb..NV-1 stay zero for the whole solve)
@@ -332,13 +338,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
   auto block_bytes = [&](int s) -> uint32_t {
     return (uint32_t)((long long)(s == Lc ? geo.LBM : geo.LB) * sizeof(T));
   };
-  int issued = 0;   // copies issued (thread 0's count)
-  if (tid == 0)
-    for (; issued < NBUF && issued < nseq; ++issued) {
-      mbar_expect_tx(&bars[issued], block_bytes(issued));
-      bulk_g2s(ring + (long long)issued * geo.LBM, src + block_off(issued), block_bytes(issued),
-               &bars[issued]);
+  int issued = 0;   // copies issued (thread 0's count; split: inverses)
+  int cissued = 0;  // split: couplings issued
+  auto issue_S = [&](int s) {   // split: the symmetric inverse of step s's block
+    const uint32_t bytes = (uint32_t)((long long)geo.TB * sizeof(T));
+    mbar_expect_tx(&bars[0], bytes);
+    bulk_g2s(ring, src + block_off(s), bytes, &bars[0]);
+    ++issued;
+  };
+  auto issue_C = [&](int s) {   // split: the coupling(s) of step s's block
+    const uint32_t bytes = (uint32_t)((s == Lc ? 12LL : 6LL) * nb * sizeof(T));
+    mbar_expect_tx(&bars[1 + (s & 1)], bytes);
+    bulk_g2s(cbuf + (long long)(s & 1) * 12 * nb, src + block_off(s) + geo.TB, bytes, &bars[1 + (s & 1)]);
+    ++cissued;
+  };
+  if (tid == 0) {
+    if constexpr (SPLIT) {
+      issue_S(0);
+      issue_C(0);
+      if (nseq > 1) issue_C(1);
+    } else {
+      for (; issued < NBUF && issued < nseq; ++issued) {
+        mbar_expect_tx(&bars[issued], block_bytes(issued));
+        bulk_g2s(ring + (long long)issued * geo.LBM, src + block_off(issued), block_bytes(issued),
+                 &bars[issued]);
+      }
     }
+  }
   uint32_t phase = 0u;   // bit b: parity of the next wait on stage b
 
   // vector phases: (node a, right-hand side jj) pairs q = tid + s NTH, s < TPF
@@ -593,39 +619,55 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
     }
     phase ^= 1u << b;
   };
-  wait_stage(0);
+  auto wait_bar = [&](int b, uint32_t parity) {   // split: thread 0, before a barrier
+    if (tid == 0 && !s_abort && !mbar_wait(&bars[b], parity)) {
+      s_abort = 1;
+      atomicExch(err, (int)MSTOPO_TIMEOUT);
+    }
+  };
+  auto wait_S = [&](int s) { wait_bar(0, (uint32_t)(s & 1)); };
+  auto wait_C = [&](int s) { wait_bar(1 + (s & 1), (uint32_t)((s >> 1) & 1)); };
+  // split: the next step's inverse, once every read of this one is behind a barrier
+  auto refill_S = [&](int s) {
+    if constexpr (SPLIT)
+      if (tid == 0 && s + 1 < nseq && !s_abort) issue_S(s + 1);
+  };
+  if constexpr (!SPLIT) wait_stage(0);
   __syncthreads();
   for (int s = 0; s < nseq; ++s) {
-    if constexpr (NBUF == 1) {   // one stage: block s was issued at the end of step s - 1
-      if (s > 0) {
-        wait_stage(s);
-        __syncthreads();
-      }
+    if constexpr (SPLIT) {
+      // the coupling (issued a step ahead) and, for a backward line (product first), the inverse
+      wait_C(s);
+      if (s > Lc) wait_S(s);
+      __syncthreads();
     }
     if (s_abort) { abort = true; break; }
     const T* L = ring + (long long)(s % NBUF) * geo.LBM;
+    const T* Cs = SPLIT ? cbuf + (long long)(s & 1) * 12 * nb : L + geo.TB;   // coupling(s) of the block
     if (s < Lc) {
       // forward chain line j: t = b - C_j w_{j-1}, w_j = S_j^-1 t
       const int j = s, l = line_of(j);
       if (j > 0) {
-        couple(L + geo.TB, vp, T(-1), true, vt);
+        couple(Cs, vp, T(-1), true, vt);
       } else {
 #pragma unroll
         for (int q = 0; q < TPF; ++q)
           if (qv[q]) *reinterpret_cast<V2*>(vt + qj[q] * NV + 2 * qa[q]) = pf[q];
       }
       gather(j + 1 < Lc ? line_of(j + 1) : Lc, pf);   // next line's input (the middle line last)
+      if constexpr (SPLIT) wait_S(s);
       __syncthreads();
       product(L);
       if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
       __syncthreads();
+      refill_S(s);
       // w_j (in vy) to the work buffer for the backward sweep (the last one stays in shared
       // memory: the first backward line rewrites that slot); it becomes w_{j-1} of the next line
       if (j + 1 < Lc) store_line(l, vy);
       T* tmp = vp; vp = vy; vy = tmp;
     } else if (s == Lc) {
       // middle line: u = C_mid w_{Lc-1} published, then x_m = M^-1 (b_m - u_0 - u_1) in both CTAs
-      const T* Cown = L + geo.TB + rank * 6 * nb;
+      const T* Cown = Cs + rank * 6 * nb;
       couple(Cown, vp, T(1), false, vu);
       cluster.sync();   // both contributions are in shared memory
       met = true;
@@ -643,9 +685,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
         *reinterpret_cast<V2*>(vt + o) = t;
         wk[q] = *reinterpret_cast<const V2*>(vp + o);   // w_{Lc-1} for the first backward line
       }
+      if constexpr (SPLIT) wait_S(s);
       __syncthreads();
       product(L);
       __syncthreads();
+      refill_S(s);
       if (rank == 0) store_line(Lc, vy);
       couple_t(Cown, vy, vt);   // t of chain line Lc - 1
       if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
@@ -655,6 +699,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
       const int j = 2 * Lc - s, l = line_of(j);
       product(L);
       __syncthreads();
+      refill_S(s);
 #pragma unroll
       for (int q = 0; q < TPF; ++q) {
         if (!qv[q]) continue;
@@ -668,21 +713,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * TMAXW, MINB) k_
       }
       if (j > 0) load_w(line_of(j - 1), wk);
       __syncthreads();
-      if (j > 0) couple_t(L + geo.TB, vw, vt);
+      if (j > 0) couple_t(Cs, vw, vt);
       if (NBUF > 1 && s + 1 < nseq) wait_stage(s + 1);
       __syncthreads();
     }
-    // every read of stage s % NBUF is behind a barrier: refill it with block s + NBUF
-    if (tid == 0 && issued < nseq && !s_abort) {
-      const int st = issued % NBUF;
-      mbar_expect_tx(&bars[st], block_bytes(issued));
-      bulk_g2s(ring + (long long)st * geo.LBM, src + block_off(issued), block_bytes(issued),
-               &bars[st]);
-      ++issued;
+    if constexpr (SPLIT) {
+      // every read of this step's coupling buffer is behind a barrier: the coupling two steps on
+      if (tid == 0 && s + 2 < nseq && !s_abort) issue_C(s + 2);
+    } else {
+      // every read of stage s % NBUF is behind a barrier: refill it with block s + NBUF
+      if (tid == 0 && issued < nseq && !s_abort) {
+        const int st = issued % NBUF;
+        mbar_expect_tx(&bars[st], block_bytes(issued));
+        bulk_g2s(ring + (long long)st * geo.LBM, src + block_off(issued), block_bytes(issued),
+                 &bars[st]);
+        ++issued;
+      }
     }
   }
   if (!met) cluster.sync();   // the partner meets this CTA at the middle line in any case
-  if (abort && tid == 0) {
+  if (SPLIT && abort && tid == 0) {
+    // every copy issued lands before the CTA exits (waits on completed phases return at once)
+    if (issued > 0 && !tri_wait(&bars[0], (uint32_t)((issued - 1) & 1))) atomicExch(err, (int)MSTOPO_TIMEOUT);
+    for (int c = cissued - 1; c >= 0 && c >= cissued - 2; --c)
+      if (!tri_wait(&bars[1 + (c & 1)], (uint32_t)((c >> 1) & 1))) atomicExch(err, (int)MSTOPO_TIMEOUT);
+  }
+  if (!SPLIT && abort && tid == 0) {
     // every copy issued and not yet waited for lands before the CTA exits
     for (int m2 = 0; m2 < NBUF; ++m2) {
       const int last = issued - 1 - m2;    // copy `last` went to stage last % NBUF
@@ -712,7 +768,9 @@ static int tri_threads(int nb) {
 
 static size_t patch_tri_smem(int nb, int R, int nbuf, size_t elem) {
   const TriGeom g = tri_geometry(nb, 3);
-  return ((size_t)nbuf * g.LBM + 6 * (size_t)g.NV * R) * elem;
+  // one stage: the inverse part [TB] and two coupling buffers [2][12 nb]
+  const size_t blocks = nbuf == 1 ? (size_t)g.TB + 24 * (size_t)nb : (size_t)nbuf * g.LBM;
+  return (blocks + 6 * (size_t)g.NV * R) * elem;
 }
 
 long long patch_tri_system_elems(int nb, int NL) { return tri_geometry(nb, NL).SS; }
