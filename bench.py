@@ -637,7 +637,9 @@ def run_workload(args):
         torch.cuda.synchronize()
         tq = time.time() - t
         its = [i[0]["iterations"] for i in infos]
+        one_graph = all(p.stats()["batch_graph_solves"] >= 2 for p in probs)
         out.update({"instances": len(probs), "dofs": dofs, "build_s": tb,
+                    "batch_one_graph_launch": one_graph,
                     "coarse_solvers": sorted(set(b["coarse_solver"] for b in binfo)),
                     "batch_solve_s": ts, "batch_mdof_per_s": dofs / ts / 1e6,
                     "sequential_solve_s": tq, "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],

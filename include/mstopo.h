@@ -221,10 +221,14 @@ mstopo_status mstopo_solve_host(mstopo_handle* h, int32_t realisation, const dou
  * handle and stream, so their kernels overlap on the GPU.  Handles must be distinct and
  * should not share a stream (a shared stream serialises them).  The builds run from up to
  * 16 host threads (a build waits for the GPU between its steps).  The solves run from the
- * calling thread alone: every instance's whole solve (one CUDA graph launch with device-side
- * convergence tests) is enqueued first, then the instances are finished in turn, so the
- * batch is one launch sequence with one wait per instance at its end.  Handles with graphs
- * off or per-kernel profiling on solve one after the other.
+ * calling thread alone, as one CUDA graph launch for the whole batch: every instance's whole
+ * solve (its start, its flexible-CG loop as WHILE/IF conditional nodes with device-side
+ * convergence tests, its outputs) is captured into one graph as an independent branch, the
+ * graph runs once, and the instances are finished in turn (mstopo_stats.batch_graph_solves
+ * counts these).  When an instance cannot take part (graphs off, per-kernel profiling on,
+ * GMRES, a rebuild pending from the update rule, another device) or a capture step is
+ * refused, every instance's solve is enqueued on its own stream instead, then finished in
+ * turn.
  * mstopo_batch_build_preconditioner: as mstopo_build_preconditioner(hs[b], ref, infos + b)
  *   for every b; infos: HOST array of n, may be NULL.
  * mstopo_batch_solve: as mstopo_solve(hs[b], -1, f[b], u[b], NULL, infos + 4 b) for every
@@ -434,6 +438,8 @@ typedef struct {
   int64_t device_loop_solves;  /* solves of this handle whose iteration loop ran as one CUDA
                                   graph with device-side convergence tests (the others ran a
                                   host-driven loop: graphs off or per-kernel profiling on) */
+  int64_t batch_graph_solves;  /* mstopo_batch_solve calls in which this handle's whole solve
+                                  ran inside the batch's single graph launch                  */
 } mstopo_stats;
 
 /* Turn per-kernel event timing on (1) or off (0) for this handle; resets its counters.

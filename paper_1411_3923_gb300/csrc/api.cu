@@ -513,6 +513,7 @@ mstopo_status mstopo_get_stats(mstopo_handle* h, mstopo_stats* out) {
   out->base_iterations = h->base_iters;
   out->rebuild_pending = h->rebuild_pending;
   out->device_loop_solves = h->device_loop_solves;
+  out->batch_graph_solves = h->batch_graph_solves;
   for (int k = 0; k < 4; ++k) {
     out->kernel_launches[k] = h->prof.n[k];
     out->kernel_ms[k] = h->prof.ms[k];
@@ -576,10 +577,78 @@ mstopo_status mstopo_batch_solve(mstopo_handle* const* hs, int32_t n, const doub
   mstopo_status st0 = check_batch(hs, n);
   if (st0 != MSTOPO_OK) return st0;
   if (!f || !u) return MSTOPO_INVALID_ARG;
+  std::vector<mstopo_status> st(n, MSTOPO_OK);
+  // One graph launch for the whole batch: every instance's solve (its start, its device-side
+  // flexible-CG loop with WHILE/IF nodes, its outputs) is captured into one graph as an
+  // independent branch, and the graph runs once.  It needs every instance on the device-side
+  // loop (graphs on, no per-kernel profiling, flexible CG) on one device with its solver
+  // workspace allocated; otherwise, or if any capture step is refused, the instances are
+  // enqueued one after another below.
+  bool one_graph = n > 0;
+  for (int b = 0; b < n && one_graph; ++b) {
+    mstopo_handle* h = hs[b];
+    one_graph = h->graphs_enabled && !h->prof.on && !h->loop_graph_failed &&
+                h->p.krylov == MSTOPO_KRYLOV_FCG && h->device == hs[0]->device &&
+                h->design_ready && h->pc.built &&
+                !(h->p.reuse_preconditioner && h->p.rebuild_ratio > 0.0 && h->rebuild_pending);
+  }
+  if (one_graph) {
+    cudaSetDevice(hs[0]->device);
+    for (int b = 0; b < n && one_graph; ++b) one_graph = solver_alloc(hs[b]) == MSTOPO_OK;
+  }
+  if (one_graph) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    int captured = 0;
+    std::vector<long long> dls(n);
+    for (int b = 0; b < n; ++b) dls[b] = hs[b]->device_loop_solves;
+    for (int b = 0; b < n && ok; ++b) {
+      mstopo_handle* h = hs[b];
+      if (cudaStreamBeginCaptureToGraph(h->s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      h->batch_graph = g;
+      st[b] = solve_start(h, -1, f[b], u[b], nullptr);
+      h->batch_graph = nullptr;
+      cudaGraph_t out = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(h->s, &out);
+      if (st[b] != MSTOPO_OK || ee != cudaSuccess) ok = false;
+      ++captured;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    cudaEvent_t done = nullptr;
+    if (ok) ok = cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaGraphLaunch(ex, hs[0]->s) == cudaSuccess && cudaEventRecord(done, hs[0]->s) == cudaSuccess;
+    // every instance's stream waits for the graph, so that its finish sees the results
+    for (int b = 0; b < n && ok; ++b) ok = cudaStreamWaitEvent(hs[b]->s, done, 0) == cudaSuccess;
+    if (ok) {
+      for (int b = 0; b < n; ++b) {
+        mstopo_status sb = solve_finish(hs[b], -1, infos ? infos + (size_t)b * MSTOPO_MAX_SYS : nullptr);
+        if (st[b] == MSTOPO_OK) st[b] = sb;
+      }
+      for (int b = 0; b < n; ++b) hs[b]->batch_graph_solves++;
+    }
+    if (done) cudaEventDestroy(done);
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    if (ok) {
+      for (int b = 0; b < n; ++b)
+        if (st[b] != MSTOPO_OK) return st[b];
+      return MSTOPO_OK;
+    }
+    // refused: forget the captured starts and take the per-instance path
+    cudaGetLastError();
+    for (int b = 0; b < captured; ++b) {
+      hs[b]->sv.run_pending = 0;
+      hs[b]->device_loop_solves = dls[b];
+      st[b] = MSTOPO_OK;
+    }
+  }
   // One host thread: every instance's solve is enqueued on its own stream first (with the
   // device-side loop each is a few launches and one graph launch, none waiting for the GPU),
   // then each is finished in turn; the GPU runs the instances concurrently meanwhile.
-  std::vector<mstopo_status> st(n, MSTOPO_OK);
   for (int b = 0; b < n; ++b) {
     cudaSetDevice(hs[b]->device);
     st[b] = solve_start(hs[b], -1, f[b], u[b], nullptr);

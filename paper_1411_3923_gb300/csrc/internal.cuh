@@ -257,6 +257,11 @@ struct mstopo_handle {
   long long device_loop_solves = 0;   // solves that ran the device-side loop
   int patch_tc = -1;                  // FP32 patch solves on the tensor cores: -1 by problem size, 0 off, 1 on
   int autotune = 0;                   // MSTOPO_EXEC_AUTOTUNE: time the patch-solve configurations
+  // set while mstopo_batch_solve captures this handle's whole solve into one batch graph:
+  // fcg_start then builds its device-side loop as nodes of that graph instead of launching
+  // its own loop graph
+  cudaGraph_t batch_graph = nullptr;
+  long long batch_graph_solves = 0;   // batch solves that ran inside one graph launch
   int inject = 0;                     // test injection (mstopo_inject), consumed by its target
   long long builds = 0;               // preconditioner builds (explicit and automatic)
   int base_iters = -1;                // iterations of the first solve after the last build

@@ -454,7 +454,10 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
   const bool mixed = h->p.precision != MSTOPO_FP64;
   const double tol2 = h->p.tol * h->p.tol;
   sv.run_pending = 0;
-  CK(cudaEventRecord(sv.ev0, h->s));
+  // inside a batch capture the timing events become event-record nodes of the batch graph
+  const bool in_batch = h->batch_graph != nullptr;
+  const unsigned ev_flags = in_batch ? cudaEventRecordExternal : cudaEventRecordDefault;
+  CK(cudaEventRecordWithFlags(sv.ev0, h->s, ev_flags));
   CK(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), h->s));   // device-wait timeout word
   // f (same load for every system), masked; x0
   for (int s = 0; s < nsys; ++s) CK(launch_mask_copy(f, sv.f + s * n, h->d_nmask, h->n_nodes, 1, n, h->s));
@@ -534,13 +537,15 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
   };
   // ---- the whole loop as one graph (no host round trip inside the solve) ----
   bool looped = false;
-  if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed) {
-    FcgGraph& gr = h->fcg_graph;
-    auto build_loop = [&]() -> cudaError_t {
-      cudaGraph_t top = nullptr;
-      cudaError_t e = cudaGraphCreate(&top, 0);
-      if (e != cudaSuccess) return e;
-      struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{top};
+  FcgGraph& gr = h->fcg_graph;
+  // The loop as a graph: into == nullptr builds and instantiates the handle's own loop graph;
+  // otherwise h->s is capturing into `into` (a batch graph) and the loop becomes nodes of it:
+  // the capture pauses at the WHILE node while the bodies are captured, then resumes after it.
+  auto build_loop = [&](cudaGraph_t into) -> cudaError_t {
+      cudaGraph_t top = into;
+      cudaError_t e = cudaSuccess;
+      if (!into && (e = cudaGraphCreate(&top, 0)) != cudaSuccess) return e;
+      struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{into ? nullptr : top};
       cudaGraphConditionalHandle wh, ih;
       if ((e = cudaGraphConditionalHandleCreate(&wh, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
       if ((e = cudaGraphConditionalHandleCreate(&ih, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
@@ -552,7 +557,8 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
       wp.conditional.type = cudaGraphCondTypeWhile;
       wp.conditional.size = 1;
       // the loop's start (done flags, reference residuals, the WHILE condition), then the node
-      if ((e = cudaStreamBeginCaptureToGraph(h->s, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      if (!into && (e = cudaStreamBeginCaptureToGraph(h->s, top, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return e;
       k_fcg_loop_init<<<1, 32, 0, h->s>>>(sv.sc, nsys, wh);
       cudaGraphNode_t wnode = nullptr;
@@ -621,17 +627,21 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
       if (ee != cudaSuccess) return ee;
       const long long l2 = g_launch_count.load();
       g_launch_count.fetch_sub(l2 - l0);   // counted per executed pass below
-      if ((e = cudaGraphInstantiate(&gr.loop, top, 0)) != cudaSuccess) { gr.loop = nullptr; return e; }
       gr.loop_launches = l1 - l0;
       gr.true_launches = l2 - l1;
+      if (into) {   // resume the batch capture after the WHILE node
+        return cudaStreamBeginCaptureToGraph(h->s, into, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+      }
+      if ((e = cudaGraphInstantiate(&gr.loop, top, 0)) != cudaSuccess) { gr.loop = nullptr; return e; }
       gr.loop_sys0 = sys0;
       gr.loop_nsys = nsys;
       gr.loop_generation = h->pc_generation;
       return cudaSuccess;
-    };
+  };
+  if (!in_batch && h->graphs_enabled && !h->prof.on && !h->loop_graph_failed) {
     if (!gr.loop || gr.loop_sys0 != sys0 || gr.loop_nsys != nsys || gr.loop_generation != h->pc_generation) {
       if (gr.loop) { cudaGraphExecDestroy(gr.loop); gr.loop = nullptr; }
-      if (build_loop() != cudaSuccess) {
+      if (build_loop(nullptr) != cudaSuccess) {
         // conditional graph nodes unavailable: the host-driven loop below takes over
         cudaGetLastError();
         h->loop_graph_failed = 1;
@@ -639,7 +649,19 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
     }
   }
   int* h_ints = reinterpret_cast<int*>(sv.h_comp + MSTOPO_MAX_SYS);   // loop passes [2], werr
-  if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed && h->fcg_graph.loop) {
+  if (in_batch) {
+    // the loop as nodes of the batch graph being captured
+    looped = true;
+    h->device_loop_solves++;
+    CK(cudaMemsetAsync(sv.loopstat, 0, 2 * sizeof(int), h->s));
+    if (build_loop(h->batch_graph) != cudaSuccess) {
+      h->err = "batch graph: the flexible-CG loop could not be captured";
+      return MSTOPO_CUDA_ERROR;
+    }
+    CK(cudaMemcpyAsync(sv.h_sc, sv.sc, nsys * sizeof(FcgScalars), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h_ints, sv.loopstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h_ints + 2, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  } else if (h->graphs_enabled && !h->prof.on && !h->loop_graph_failed && h->fcg_graph.loop) {
     // one graph launch; nothing returns to the host before fcg_finish
     looped = true;
     h->device_loop_solves++;
@@ -746,7 +768,7 @@ mstopo_status fcg_start(mstopo_handle* h, int sys0, int nsys, const double* f, d
     }
     if (total_iters > h->p.max_iter + chunk) break;
   }
-  CK(cudaEventRecord(sv.ev1, h->s));
+  CK(cudaEventRecordWithFlags(sv.ev1, h->s, ev_flags));
   // outputs
   CK(cudaMemcpyAsync(u, sv.x, (size_t)nsys * n * 8, cudaMemcpyDeviceToDevice, h->s));
   // compliance f^T u

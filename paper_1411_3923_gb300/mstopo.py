@@ -54,7 +54,7 @@ class _Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("kernel_launches", C.c_int64 * 4),
                 ("kernel_ms", C.c_double * 4), ("builds", C.c_int64),
                 ("base_iterations", C.c_int32), ("rebuild_pending", C.c_int32),
-                ("device_loop_solves", C.c_int64)]
+                ("device_loop_solves", C.c_int64), ("batch_graph_solves", C.c_int64)]
 
 
 COARSE_SOLVERS = {"auto": 0, "dense": 1, "blocktri": 2}
@@ -337,7 +337,8 @@ class Problem:
 
 def _stats_dict(st: "_Stats") -> dict:
     out = {"launches": st.launches, "builds": st.builds, "base_iterations": st.base_iterations,
-           "rebuild_pending": st.rebuild_pending, "device_loop_solves": st.device_loop_solves}
+           "rebuild_pending": st.rebuild_pending, "device_loop_solves": st.device_loop_solves,
+           "batch_graph_solves": st.batch_graph_solves}
     for name, k in KERNEL_IDS.items():
         out[name] = {"launches": st.kernel_launches[k], "ms": st.kernel_ms[k]}
     return out
@@ -394,8 +395,10 @@ def batch_build_preconditioner(problems, ref: int = -1) -> list:
 
 
 def batch_solve(problems, fs):
-    """Solve all realisations of independent problems concurrently (one stream and host
-    thread per problem).  fs: one device load vector per problem.  Returns (us, infos)."""
+    """Solve all realisations of independent problems concurrently: one graph launch for the
+    whole batch, every problem an independent branch with its device-side loop (else one
+    launch sequence per problem from this thread).  fs: one device load vector per problem.
+    Returns (us, infos)."""
     n = len(problems)
     fs = [_dev(f) for f in fs]
     us = [torch.empty((p.n_eta, p.nely + 1, p.nelx + 1, 2), dtype=torch.float64, device=f.device)

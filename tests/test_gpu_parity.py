@@ -334,9 +334,12 @@ def test_mixed_solve_with_tensor_core_patches(H):
 
 
 def test_batch_solve_matches_single_solves_and_oracle():
-    """Independent problems of uneven sizes solved concurrently (one stream and host thread
-    each): every instance equals its own single solve bit for bit (same kernels, fixed
-    reduction order) and the oracle's direct solve."""
+    """Independent problems of uneven sizes solved concurrently: every instance's whole solve,
+    its device-side loop included, runs inside one graph launch for the batch (checked by the
+    handles' batch_graph_solves counters); every instance equals its own single solve bit for
+    bit (same kernels, fixed reduction order) and the oracle's direct solve.  With per-kernel
+    profiling on for one instance the batch takes the per-instance path and gives the same
+    results."""
     m = _gpu()
     shapes = [(48, 16, 1), (64, 32, 3), (32, 16, 1), (96, 32, 3), (64, 16, 1)]
     wls = [workloads.small(nx, ny, seed=20 + b, kind="voids", bc="cantilever", H=8, n_eig=4,
@@ -348,11 +351,22 @@ def test_batch_solve_matches_single_solves_and_oracle():
         p.set_design(cuda(wl.rho), wl.rmin, wl.beta, wl.etas, wl.cell)
         probs.append(p)
     m.batch_build_preconditioner(probs)
-    us, infos = m.batch_solve(probs, [cuda(wl.force) for wl in wls])
+    fs = [cuda(wl.force) for wl in wls]
+    g0 = [p.stats()["batch_graph_solves"] for p in probs]
+    us, infos = m.batch_solve(probs, fs)
+    assert [p.stats()["batch_graph_solves"] - g for p, g in zip(probs, g0)] == [1] * len(probs)
+    us2, infos2 = m.batch_solve(probs, fs)   # a second batch: a new graph, the same results
+    probs[1].set_profiling(True)
+    us3, infos3 = m.batch_solve(probs, fs)   # profiling on: one launch sequence per instance
+    probs[1].set_profiling(False)
+    assert [p.stats()["batch_graph_solves"] - g for p, g in zip(probs, g0)] == [2] * len(probs)
     for b, (p, wl) in enumerate(zip(probs, wls)):
         u1, inf1 = p.solve(cuda(wl.force), -1)
-        assert torch.equal(u1, us[b])
+        assert torch.equal(u1, us[b]) and torch.equal(u1, us2[b]) and torch.equal(u1, us3[b])
         assert [i["iterations"] for i in inf1] == [i["iterations"] for i in infos[b]]
+        assert [i["iterations"] for i in infos2[b]] == [i["iterations"] for i in infos3[b]] == \
+            [i["iterations"] for i in infos[b]]
+        assert all(i["ms"] > 0.0 for i in infos[b])
         ref = pipeline.run(wl, "direct", with_grad=False)
         for k, inf in enumerate(infos[b]):
             assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
