@@ -265,7 +265,10 @@ class Problem:
     def _nsys(self, realisation: int) -> int:
         return self.n_eta if realisation < 0 else 1
 
-    def solve(self, f: torch.Tensor, realisation: int = -1, u0: Optional[torch.Tensor] = None):
+    def solve(self, f: torch.Tensor, realisation: int = -1, u0: Optional[torch.Tensor] = None,
+              check: bool = True):
+        """Solve K(E_k) u_k = f; returns (u, infos).  check=False returns systems that did not
+        converge (status MAX_ITER, NOT_SPD, ...) in infos instead of raising."""
         f = _dev(f)
         ns = self._nsys(realisation)
         u = torch.empty((ns, self.nely + 1, self.nelx + 1, 2), dtype=torch.float64, device="cuda")
@@ -273,7 +276,7 @@ class Problem:
         u0p = _ptr(_dev(u0)) if u0 is not None else None
         st = _lib.mstopo_solve(self._h, realisation, _ptr(f), _ptr(u), u0p, infos)
         out = [{k: getattr(i, k) for k, _ in _SolveInfo._fields_} for i in infos]
-        if st != 0:
+        if st != 0 and (check or not any(o["iterations"] for o in out)):
             raise MstopoError(st, _lib.mstopo_last_error(self._h).decode() + f" {out}")
         return u, out
 

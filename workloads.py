@@ -143,10 +143,12 @@ def make(name: str, scale: int = 1) -> Workload:
         fixed, force = mbb_bc(nelx, nely)
         return Workload(name, nelx, nely, cell, (32, 32), fixed, force, rmin=3.0, beta=8.0,
                         etas=(0.5,), H=32, n_eig=6)
-    if name == "mbb_c3":
+    if name in ("mbb_c3", "mbb_c3_literal"):
+        # mbb_c3_literal: the layers as the configuration states them, without struts (every
+        # stiff layer floats on the void material: a mechanism up to Emin)
         rng = np.random.default_rng(3)
         nelx, nely = 2048 // scale, 1024 // scale
-        rho = layered(nelx, nely, rng)
+        rho = layered(nelx, nely, rng, strut=0 if name == "mbb_c3_literal" else 8)
         fixed, force = mbb_bc(nelx, nely)
         return Workload(name, nelx, nely, rho, None, fixed, force, rmin=3.0, beta=16.0,
                         etas=(0.3, 0.5, 0.7), H=32, n_eig=6)
