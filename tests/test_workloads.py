@@ -74,3 +74,15 @@ def test_uneven_batch():
     assert sizes <= {(256, 128), (384, 192), (512, 256), (768, 384), (1024, 512)}
     assert sum(2 * (w.nelx + 1) * (w.nely + 1) for w in batch) == 26_178_048
     assert all(w.H == 16 and w.n_eig == 4 for w in batch)
+
+
+def test_literal_layers_are_the_strut_layers_without_struts():
+    """mbb_c3_literal: the same seeded layer sequence as mbb_c3 with every void layer fully
+    void (no struts), so the stiff layers do not touch one another."""
+    lit, st = workloads.make("mbb_c3_literal", 4), workloads.make("mbb_c3", 4)
+    assert lit.rho.shape == st.rho.shape and (lit.rho <= st.rho).all()
+    rows_lit, rows_st = lit.rho.max(axis=1), st.rho.min(axis=1)
+    assert set(np.unique(lit.rho)) <= {0.0, 1.0}
+    # a row is solid in both or void in the literal layers (struts only fill void rows)
+    assert np.array_equal(rows_lit == 1.0, rows_st == 1.0)
+    assert (lit.rho[rows_lit == 0.0] == 0.0).all() and (st.rho[rows_lit == 0.0] > 0.0).any()
