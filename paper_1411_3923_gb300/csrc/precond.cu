@@ -1491,47 +1491,53 @@ mstopo_status precond_build(mstopo_handle* h, int ref, mstopo_build_info* info) 
   }
   if (tuned == 1) {
     // time one launch of every candidate (after one untimed launch) on a zero input: the
-    // kernels' time does not depend on the values
+    // kernels' time does not depend on the values; every exit frees what the timing holds
     float* r0 = nullptr;
-    CKB(cudaMalloc(&r0, (size_t)nsv * h->n_dof * sizeof(float)));
-    CKB(cudaMemsetAsync(r0, 0, (size_t)nsv * h->n_dof * sizeof(float), s));
-    cudaEvent_t t0, t1;
-    CKB(cudaEventCreate(&t0));
-    CKB(cudaEventCreate(&t1));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    PatchGroups Gt;
+    auto free_groups = [&](PatchGroups& G) {
+      dfree(G.d_perm); dfree(G.d_type); dfree(G.d_first); dfree(G.d_count); dfree(G.d_sys); dfree(G.d_agg);
+      G = PatchGroups();
+    };
     float best_ms = 0.f;
     int best_tc = 0, best_p = P;
+    cudaError_t e = cudaMalloc(&r0, (size_t)nsv * h->n_dof * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(r0, 0, (size_t)nsv * h->n_dof * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
     const int cand[4] = {4, 8, 16, TW_M};
-    for (int ci = 0; ci < 4; ++ci) {
+    bool first = true;
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
       const bool tc = cand[ci] == TW_M;
       if (tc && !pc.d_ptw) continue;
-      PatchGroups Gt;
       const PatchGroups* G = &pc.pg[tc ? 1 : 0];
       if (!tc && cand[ci] != P) {
-        CKB(build_groups(Gt, cand[ci]));
+        e = build_groups(Gt, cand[ci]);
         G = &Gt;
       }
       float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        CKB(cudaEventRecord(t0, s));
-        CKB(tc ? patch_twtc_solve(h, *G, r0, 0, nsv, pc.d_zp32, pc.d_twu)
-               : patch_tri_solve_f32(h, *G, r0, 0, nsv, pc.d_zp32));
-        CKB(cudaEventRecord(t1, s));
-        CKB(cudaEventSynchronize(t1));
-        CKB(cudaEventElapsedTime(&ms, t0, t1));
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(t0, s);
+        if (e == cudaSuccess)
+          e = tc ? patch_twtc_solve(h, *G, r0, 0, nsv, pc.d_zp32, pc.d_twu)
+                 : patch_tri_solve_f32(h, *G, r0, 0, nsv, pc.d_zp32);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
       }
-      if (G == &Gt) {
-        cudaFree(Gt.d_perm); cudaFree(Gt.d_type); cudaFree(Gt.d_first); cudaFree(Gt.d_count);
-        cudaFree(Gt.d_sys); cudaFree(Gt.d_agg);
-      }
-      if (ci == 0 || ms < best_ms) {
+      if (G == &Gt) free_groups(Gt);
+      if (e == cudaSuccess && (first || ms < best_ms)) {
         best_ms = ms;
         best_tc = tc ? 1 : 0;
         best_p = cand[ci];
+        first = false;
       }
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    cudaFree(r0);
+    free_groups(Gt);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    dfree(r0);
+    CKB(e);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune[tkey] = {best_tc, best_p};
