@@ -24,10 +24,12 @@
 // m = 32 w + lane, the first and the second half of the line's K-steps), warp 8 streams the
 // packed blocks in units of up to four K-steps and the couplings (cp.async.bulk into rings,
 // mbarrier transaction counts, L2 prefetch two blocks ahead), warp 9 issues the MMAs (one
-// lane): one readiness wait, one stage wait and one commit per unit.  Two accumulators in TMEM alternate
-// by line, so the epilogue of line s (reading accumulator s mod 2, writing the next A chunk by
-// chunk) overlaps the MMAs of line s + 1, which start on each K-step of A as soon as its chunk
-// is written.
+// lane): one readiness wait, one stage wait and one commit per unit.  Two accumulators in
+// TMEM alternate by line, so the epilogue of line s (reading accumulator s mod 2, writing the
+// next A unit by unit) overlaps the MMAs of line s + 1, which start on each unit of A as soon
+// as it is written.  Every accumulator column sums every K-step, so a line's epilogue starts
+// only after all of its MMAs: a line step is one MMA chain plus the epilogue's lead-in to its
+// first unit.
 // Every mbarrier wait is bounded; on a timeout the CTA records MSTOPO_TIMEOUT, the roles stop,
 // the copies and MMAs in flight are drained, every thread still arrives at the cluster barrier
 // once, and TMEM is released before the CTA exits.
